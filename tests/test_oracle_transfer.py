@@ -1,0 +1,112 @@
+"""Pins of the oracle's non-nested transfer P and restriction R = P^T (Sec. 2-3)."""
+import numpy as np
+import pytest
+
+from oracle import dofs, fe, transfer
+from tests.oracle_meshes import box_level, scramble
+
+
+def _level(lv, k):
+    node_of, nn, oc, ol = dofs.number_dofs(lv.cells, k, lv.dim)
+    mask = dofs.dirichlet_nodes(lv.cells, lv.dirichlet, node_of, k, lv.dim)
+    pts = dofs.support_points(lv.vertices, lv.cells, oc, ol, k, lv.dim)
+    return dict(vertices=lv.vertices, cells=lv.cells, node_of=node_of, free=~mask, pts=pts, n=nn)
+
+
+def _P(fine, coarse, k, dim):
+    free_f = np.nonzero(fine["free"])[0]
+    P, cell, xi = transfer.transfer_matrix(fine["pts"], free_f, coarse, k, dim)
+    return P, free_f, cell, xi
+
+
+@pytest.mark.parametrize("dim,nc,nf,k", [(2, 5, 11, 1), (2, 5, 11, 3), (3, 3, 7, 2), (3, 2, 5, 4)])
+def test_reproduces_linear_fields_on_jittered_non_nested_meshes(dim, nc, nf, k):
+    c = _level(box_level((nc,) * dim, alpha=0.2, seed=1, dirichlet="none"), k)
+    f = _level(box_level((nf,) * dim, alpha=0.2, seed=2, dirichlet="none"), k)
+    P, free_f, _, _ = _P(f, c, k, dim)
+    a = np.array([0.4, -0.9, 1.3][:dim])
+    u = lambda x: x @ a - 0.2
+    np.testing.assert_allclose(P @ u(c["pts"]), u(f["pts"][free_f]), atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 2), (3, 3)])
+def test_reproduces_degree_k_polynomials_on_affine_non_nested_meshes(dim, k):
+    c = _level(box_level((3,) * dim, dirichlet="none"), k)
+    f = _level(box_level((7,) * dim, dirichlet="none"), k)
+    P, free_f, _, _ = _P(f, c, k, dim)
+    rng = np.random.default_rng(k)
+    for _ in range(4):
+        e = rng.multinomial(k, [1.0 / (dim + 1)] * (dim + 1))[:dim]   # total degree <= k
+        u = lambda x: np.prod(x ** e, axis=1)
+        np.testing.assert_allclose(P @ u(c["pts"]), u(f["pts"][free_f]), atol=1e-12)
+
+
+@pytest.mark.parametrize("dim,k", [(2, 2), (3, 3)])
+def test_identical_meshes_give_identity(dim, k):
+    lv = box_level((3,) * dim, alpha=0.2, seed=4)
+    c = _level(lv, k)
+    f = _level(scramble(lv, seed=6), k)        # same geometry, other numbering/orientation
+    P, free_f, _, _ = _P(f, c, k, dim)
+    Pd = P.toarray()
+    Pd[np.abs(Pd) < 1e-12] = 0.0
+    assert np.all((Pd == 0) | (np.abs(Pd - 1) < 1e-12))
+    assert np.all((Pd != 0).sum(1) == 1) and np.all((Pd != 0).sum(0) == 1)
+    # the 1 sits at the coarse node with the same support point
+    cols = np.nonzero(c["free"])[0][Pd.argmax(1)]
+    np.testing.assert_allclose(c["pts"][cols], f["pts"][free_f], atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,k", [(2, 3), (3, 2)])
+def test_nested_meshes_give_canonical_injection(dim, k):
+    """On nested meshes P is the embedding V_{l-1} in V_l (Sec. 4.1): the fine
+    interpolant of a coarse function equals it everywhere."""
+    c = _level(box_level((2,) * dim, dirichlet="none"), k)
+    f = _level(box_level((4,) * dim, dirichlet="none"), k)
+    P, free_f, _, _ = _P(f, c, k, dim)
+    rng = np.random.default_rng(0)
+    uc = rng.standard_normal(c["n"])
+    uf = P @ uc
+    # evaluate both fields at random points of every fine cell (affine, axis-aligned cells)
+    xi = rng.random((9, dim))
+    val, _ = fe.tensor_basis(k, dim, xi)
+    for cf in range(len(f["cells"])):
+        lo = f["vertices"][f["cells"][cf][0]]
+        x = lo + xi * 0.25
+        fine_vals = val @ uf[f["node_of"][cf]]
+        cc = np.floor(x[0] / 0.5).astype(int)
+        cidx = int(sum(cc[d] * 2 ** d for d in range(dim)))
+        xc = (x - c["vertices"][c["cells"][cidx][0]]) / 0.5
+        vc, _ = fe.tensor_basis(k, dim, xc)
+        np.testing.assert_allclose(fine_vals, vc @ uc[c["node_of"][cidx]], atol=1e-12)
+
+
+def test_located_coordinates_map_back_and_lowest_cell_wins():
+    c = _level(box_level((4, 4, 3), alpha=0.2, seed=3, dirichlet="none"), 2)
+    f = _level(box_level((9, 8, 7), alpha=0.2, seed=8, dirichlet="none"), 2)
+    P, free_f, cell, xi = _P(f, c, 2, 3)
+    N, _ = fe.q1_shape(3, xi)
+    X = c["vertices"][c["cells"][cell]]
+    np.testing.assert_allclose(np.einsum("pv,pvd->pd", N, X), f["pts"][free_f], atol=1e-12)
+    assert xi.min() >= 0.0 and xi.max() <= 1.0
+    # a point on the face shared by coarse cells 0 and 1 (x-neighbours) goes to cell 0
+    face_pt = c["vertices"][c["cells"][0][[1, 3, 5, 7]]].mean(0)[None]
+    cl, _ = transfer.locate(face_pt, c["vertices"], c["cells"], 3)
+    assert cl[0] == 0
+
+
+def test_nearest_point_fallback_outside_domain():
+    c = _level(box_level((3, 3), dirichlet="none"), 1)
+    pts = np.array([[1.0 + 1e-3, 0.5], [-2e-3, -1e-3]])
+    cell, xi = transfer.locate(pts, c["vertices"], c["cells"], 2)
+    assert cell[0] == 5 and abs(xi[0, 0] - 1.0) < 1e-15 and abs(xi[0, 1] - 0.5) < 1e-12
+    assert cell[1] == 0 and np.all(xi[1] == 0.0)
+
+
+def test_restriction_is_transpose():
+    c = _level(box_level((3, 3), alpha=0.2, seed=1), 2)
+    f = _level(box_level((7, 7), alpha=0.2, seed=2), 2)
+    P, _, _, _ = _P(f, c, 2, 2)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(P.shape[1])
+    y = rng.standard_normal(P.shape[0])
+    assert abs((P @ x) @ y - x @ (P.T @ y)) < 1e-12 * np.linalg.norm(x) * np.linalg.norm(y)
