@@ -8,10 +8,14 @@ xi = F_K^{-1}(x_i) by Newton's method on the Q1 map (Sec. 3.1).
 Brute force: every coarse cell is a candidate, in index order.  A cell whose
 bounding box (widened by 1e-9 of the domain size) misses the point cannot
 contain it, so it is skipped without changing the result.  Newton starts at
-xi = (1/2, ...), runs at most 30 steps and stops once max|dxi| < 1e-14.  A
-cell accepts the point when xi lies in [-1e-10, 1 + 1e-10]^d; the first
-accepting cell wins.  If no cell accepts, the cell whose xi is nearest to
-[0,1]^d is taken and xi is projected onto [0,1]^d (Eq. closest_point).
+xi = (1/2, ...), runs at most 30 steps and stops once max|dxi| < 1e-14; it has
+inverted the map only if its last step was below 1e-10 (in a strongly
+distorted cell the iterates of a point outside it can wander into [0,1]^d
+without converging, and such an iterate is not a preimage).  A cell accepts
+the point when Newton converged and xi lies in [-1e-10, 1 + 1e-10]^d; the
+first accepting cell wins.  If no cell accepts, the converged cell whose xi is
+nearest to [0,1]^d is taken and xi is projected onto [0,1]^d (Eq.
+closest_point).
 Restriction is R = P^T (Eq. residual2).
 """
 import numpy as np
@@ -22,12 +26,18 @@ from .fe import q1_shape, tensor_basis
 ACCEPT_TOL = 1e-10
 NEWTON_MAXIT = 30
 NEWTON_STOP = 1e-14
+NEWTON_CONVERGED = 1e-10
 
 
 def newton_inverse(points, X, dim):
-    """xi with F(xi) = points for Q1 maps with corners X [P, nv, dim]; NaN if singular."""
+    """(xi, converged): Newton for F(xi) = points, Q1 maps with corners X [P, nv, dim].
+
+    xi is NaN after a singular Jacobian; converged is False unless the last
+    Newton step was below NEWTON_CONVERGED.
+    """
     P = points.shape[0]
     xi = np.full((P, dim), 0.5)
+    last = np.full(P, np.inf)
     active = np.ones(P, dtype=bool)
     for _ in range(NEWTON_MAXIT):
         if not active.any():
@@ -43,15 +53,17 @@ def newton_inverse(points, X, dim):
             if ok.any():
                 dx[ok] = np.linalg.solve(J[ok], (F - points[a])[ok][..., None])[..., 0]
         xi[a] = xi[a] - dx
-        done = ~(np.max(np.abs(dx), axis=1) >= NEWTON_STOP)     # converged or NaN
+        step = np.max(np.abs(dx), axis=1)
+        last[a] = step
+        done = ~(step >= NEWTON_STOP)                           # converged or NaN
         active[a[done]] = False
-    return xi
+    return xi, last < NEWTON_CONVERGED
 
 
-def _dist_to_unit(xi):
+def _dist_to_unit(xi, converged):
     clamped = np.clip(xi, 0.0, 1.0)
     d = np.sqrt(np.sum((xi - clamped) ** 2, axis=1))
-    return np.where(np.isfinite(d), d, np.inf)
+    return np.where(np.isfinite(d) & converged, d, np.inf)
 
 
 def locate(points, coarse_vertices, coarse_cells, dim, chunk=2048):
@@ -69,8 +81,8 @@ def locate(points, coarse_vertices, coarse_cells, dim, chunk=2048):
         inside = np.all((pts[:, None, :] >= lo[None]) & (pts[:, None, :] <= hi[None]), axis=2)
         pi, ci = np.nonzero(inside)                         # row-major: cells ascending per point
         if len(pi):
-            x = newton_inverse(pts[pi], X[ci], dim)
-            ok = np.all((x >= -ACCEPT_TOL) & (x <= 1.0 + ACCEPT_TOL), axis=1)
+            x, conv = newton_inverse(pts[pi], X[ci], dim)
+            ok = conv & np.all((x >= -ACCEPT_TOL) & (x <= 1.0 + ACCEPT_TOL), axis=1)
             sel = np.nonzero(ok)[0]
             if len(sel):
                 up, first = np.unique(pi[sel], return_index=True)
@@ -78,8 +90,8 @@ def locate(points, coarse_vertices, coarse_cells, dim, chunk=2048):
                 xi[p0 + up] = x[sel[first]]
     # nearest-point fallback (Sec. 3.3): search all cells
     for p in np.nonzero(cell < 0)[0]:
-        x = newton_inverse(np.repeat(points[p][None], len(X), 0), X, dim)
-        d = _dist_to_unit(x)
+        x, conv = newton_inverse(np.repeat(points[p][None], len(X), 0), X, dim)
+        d = _dist_to_unit(x, conv)
         c = int(np.argmin(d))
         if not np.isfinite(d[c]):
             raise RuntimeError("point not found")

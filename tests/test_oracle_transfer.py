@@ -110,3 +110,23 @@ def test_restriction_is_transpose():
     x = rng.standard_normal(P.shape[1])
     y = rng.standard_normal(P.shape[0])
     assert abs((P @ x) @ y - x @ (P.T @ y)) < 1e-12 * np.linalg.norm(x) * np.linalg.norm(y)
+
+
+def test_located_points_are_true_preimages_in_distorted_cells():
+    """Deformed cube, Q4: in strongly distorted coarse cells Newton can wander
+    into [0,1]^3 without converging for points outside the cell; only a
+    converged inversion (Sec. 3.1) may be accepted, so every located xi maps
+    back to its point."""
+    from synthetic import config_levels
+    c_lv, f_lv = config_levels("c3_3d_q4_deformed", n_levels=2)
+    fn, fnn, oc, ol = dofs.number_dofs(f_lv.cells, 4, 3)
+    pts = dofs.support_points(f_lv.vertices, f_lv.cells, oc, ol, 4, 3)
+    cell, xi = transfer.locate(pts, c_lv.vertices, c_lv.cells, 3)
+    N, _ = fe.q1_shape(3, xi)
+    X = c_lv.vertices[c_lv.cells[cell]]
+    np.testing.assert_allclose(np.einsum("pv,pvd->pd", N, X), pts, rtol=0, atol=1e-12)
+    # the non-converged iterates exist: Newton from the centre of coarse cell 8
+    # does not converge for one of these points
+    p = pts[np.argmin(np.linalg.norm(pts - np.array([0.26927729, 0.71235964, 0.08251205]), axis=1))]
+    _, conv = transfer.newton_inverse(p[None], c_lv.vertices[c_lv.cells[[8]]], 3)
+    assert not conv[0]
