@@ -1,0 +1,347 @@
+"""Benchmark: solved DoF/s of one multigrid-preconditioned CG solve on GB300.
+
+Workload (one "step" = one nnmg_pcg_solve of all right-hand sides to a 1e-8
+relative residual): 3D Poisson on the unit cube, Q2, four independently
+jittered non-nested hex levels (6^3, 13^3, 27^3, 55^3 cells, +-0.15h, seeds
+1-4), f = 1 plus seven N(0,1) right-hand sides (seeds 1001-1007), Chebyshev
+degree 3 around Jacobi, FP64 direct coarse solve, V-cycle in FP32 inside FP64
+CG.  Inputs (mesh hierarchy and right-hand sides) are resident in HBM when the
+timed region starts; the working set (~1 GB of vectors and metric terms) is
+far larger than the 129 MB L2, so no flush is needed between steps.
+
+Also reported: the same solve with the V-cycle in FP64 (plain FP64 GPU
+multigrid), V-cycle and operator GDoF/s, p50/p99 solve latency, the roofline
+of the dominant kernel, the end-to-end number through the host-buffer C call,
+and the FP64 CPU oracle timed on a bounded sample of the same workload.
+
+Multi-GPU: replicas only (one independent solve per rank, weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solved DoF/s at 1e-8 rel. residual, FP32-MG vs FP64-MG; V-cycle GDoF/s; p50/p99"
+UNIT = "DoF/s"
+CONFIG = "c2_3d_q2"
+WORKLOAD = ("3D Poisson unit cube, Q2, 4 non-nested jittered hex levels 6^3/13^3/27^3/55^3 "
+            "(+-0.15h, seeds 1-4), f=1 + 7 N(0,1) RHS, Chebyshev(3)-Jacobi, FP64 direct coarse, "
+            "FP32 V-cycle in FP64 PCG, rtol 1e-8")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 CUDA-core peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _peaks():
+    try:
+        with open(PEAKS) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _rhs(n_rows, free_mask_rows, H, top, nrhs):
+    import numpy as np
+    import torch
+    from synthetic import normal_rhs
+    b = torch.zeros(n_rows, nrhs, dtype=torch.float64, device="cuda")
+    H.load_vector(top, np.ones(1), b, col=0)              # f = 1
+    if nrhs > 1:
+        r = normal_rhs(n_rows, [1000 + j for j in range(1, nrhs)])
+        r[~free_mask_rows] = 0.0
+        b[:, 1:] = torch.tensor(r, device="cuda")
+    return b
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.p = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.p is None:
+            return out
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def kernels_per_solve(n_levels, cheb, iters):
+    """Kernel launches of one PCG solve: init 2, per iteration the V-cycle
+    (per level above the coarsest: 1 + 2(m-1) pre, 2 residual, 2 restriction,
+    1 prolongation, 2m post; 1 coarse solve) plus 9 CG kernels (cast, two dots,
+    beta, p, operator, alpha, update, check)."""
+    per_level = 1 + 2 * (cheb - 1) + 2 + 2 + 1 + 2 * cheb
+    return 2 + iters * ((n_levels - 1) * per_level + 1 + 9)
+
+
+def cpu_baseline_sample(nrhs_sample=1, quiet=True):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload in
+    a single-threaded subprocess: the three coarsest levels of the same family
+    (finest 27^3 Q2 cells), f = 1, FP32 V-cycle inside FP64 CG."""
+    code = r"""
+import json, sys, time, numpy as np
+sys.path.insert(0, %r)
+from synthetic import config_levels
+from oracle.hierarchy import OracleHierarchy
+lv = config_levels("c2_3d_q2", n_levels=3)
+H = OracleHierarchy(lv, 2, cheb_degree=3)
+top = len(H.levels) - 1
+b = H.load_vector(top, lambda x: np.ones((len(x), 1)))
+B = np.stack([b] * %d, axis=1)
+t = time.perf_counter()
+x, its, rel, tr = H.pcg(B, "fp32", rtol=1e-8)
+dt = time.perf_counter() - t
+print(json.dumps({"seconds": dt, "free": int(H.levels[top].free_dofs.size), "nrhs": %d,
+                  "iters": [int(i) for i in its]}))
+""" % (ROOT, nrhs_sample, nrhs_sample)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    v = d["free"] * d["nrhs"] / d["seconds"]
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 numpy/scipy oracle, single thread, same family with the 3 coarsest "
+                       f"levels (finest 27^3 Q2 cells, {d['free']} free DoFs), {d['nrhs']} RHS f=1, "
+                       f"FP32 V-cycle in FP64 PCG to 1e-8, {d['iters']} iterations, "
+                       f"{d['seconds']:.1f} s")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline_sample(1)
+        vals.append(last["value"])
+    v = statistics.mean(vals)
+    ms = 1e3 * (last and float(last["sample"].split(", ")[-1].split(" s")[0]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle: bounded sample)"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": v,
+                             "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2412_10910_gb300 import _abi, nnmg
+    from synthetic import config_levels
+    from synthetic.meshes import CONFIGS
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    cfg = CONFIGS[CONFIG]
+    levels = config_levels(CONFIG)
+    nrhs = cfg["nrhs"]
+    H = nnmg.Hierarchy(levels, cfg["degree"], 1, cheb_degree=cfg["cheb"], max_nrhs=16)
+    top = H.n_levels - 1
+    n_nodes, n_free, n_cells = H.info(top)
+    rows = H.rows(top)
+    free_rows = ~H.constrained(top)
+    b = _rhs(rows, free_rows, H, top, nrhs)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def solve(mode):
+        return H.pcg(b, x, mode=mode, rtol=1e-8, maxit=100)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        out = None
+        for e0, e1 in evs:
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+        barrier()
+        ts = [e0.elapsed_time(e1) for e0, e1 in evs]
+        return ts, out
+
+    # ---- headline: FP32 V-cycle inside FP64 CG
+    clocks = Clocks()
+    for _ in range(args.warmup):
+        solve(_abi.FP32_MG_FP64_CG)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_step = []
+    iters = None
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, its, rel = solve(_abi.FP32_MG_FP64_CG)
+        e1.record(stream)
+        per_step.append((e0, e1))
+        iters = its
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    lat = sorted(e0.elapsed_time(e1) for e0, e1 in per_step)
+    ms = total_ms / args.steps
+    dofs = n_free * nrhs
+    value = dofs * world / (ms / 1e3)
+    relres = [float(r) for r in rel]
+
+    # ---- comparator: plain FP64 multigrid
+    ts64, (st64, its64, rel64) = timed(lambda: solve(_abi.FP64_MG), max(2, args.steps // 3), 1)
+    ms64 = max_over_ranks(statistics.mean(ts64))
+
+    # ---- V-cycle and operator throughput (fine level, all RHS)
+    r32 = torch.randn(rows, nrhs, dtype=torch.float32, device="cuda")
+    z32 = torch.empty_like(r32)
+    tv, _ = timed(lambda: H.vcycle(r32, z32), 10, 3)
+    x64 = torch.randn(rows, nrhs, dtype=torch.float64, device="cuda")
+    y64 = torch.empty_like(x64)
+    top64, _ = timed(lambda: H.apply(top, x64, y64), 10, 3)
+    x32 = x64.float()
+    y32 = torch.empty_like(x32)
+    top32, _ = timed(lambda: H.apply(top, x32, y32), 10, 3)
+
+    # ---- end to end through the host-buffer C call
+    bh = torch.empty(rows * nrhs, dtype=torch.float64, pin_memory=True)
+    bh.copy_(b.reshape(-1).cpu())
+    xh = torch.empty_like(bh)
+    for _ in range(2):
+        H.pcg_host(bh, xh, nrhs)
+    barrier()
+    t0 = time.perf_counter()
+    ke = max(2, args.steps // 2)
+    for _ in range(ke):
+        H.pcg_host(bh, xh, nrhs)
+    barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ke)
+
+    # ---- roofline of the dominant kernel: the FP64 fine-level operator (ALU bound)
+    n1 = cfg["degree"] + 1
+    fma_cell_rhs = 12 * n1 ** 4 + 9 * n1 ** 3   # 12 line sweeps of n1^4 FMA + metric
+    flops = 2.0 * fma_cell_rhs * n_cells * nrhs
+    op64_ms = statistics.mean(top64)
+    achieved = flops / (op64_ms / 1e3) / 1e12
+    peaks, peak_kind = _peaks()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "fine_free_dofs": n_free, "nrhs": nrhs,
+                   "levels": [list(lv.n) for lv in levels], "parallelism": f"replicas{world}",
+                   "l2": "working set > L2 (no flush)"},
+        "iterations": [int(i) for i in iters], "relres": relres,
+        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "fp64_mg": {"value": dofs * world / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                    "iterations": [int(i) for i in its64]},
+        "vcycle_gdofs": dofs / (statistics.mean(tv) / 1e3) / 1e9,
+        "operator_gdofs": {"f32": n_nodes * nrhs / (statistics.mean(top32) / 1e3) / 1e9,
+                           "f64": n_nodes * nrhs / (op64_ms / 1e3) / 1e9},
+        "roofline": {"kernel": "op3d_kernel<2,double,1> (FP64 fine-level operator, 8 RHS)",
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
+        "e2e": {"value": dofs * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": rows * nrhs * 8, "d2h_bytes_per_step": rows * nrhs * 8},
+        "gpu_launches": kernels_per_solve(H.n_levels, cfg["cheb"], int(max(iters))) * args.steps,
+        "clocks": clk,
+        "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_kind": peak_kind,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    H.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

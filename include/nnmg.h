@@ -1,0 +1,208 @@
+/*
+ * nnmg.h - C interface of the GB300 non-nested matrix-free multigrid library.
+ *
+ * The library solves A_L u = f (Sec. 2, Eq. linear_system) for continuous
+ * Q_k Lagrange elements (k = 1..4) on quadrilateral or hexahedral meshes with
+ * conjugate gradients preconditioned by one non-nested multigrid V-cycle
+ * (Sec. 2, Algorithm 1; Sec. 4 solver settings).  Levels are independent
+ * meshes of the same domain (Sec. 2: T_{l-1} is not contained in T_l); the
+ * transfer between them evaluates coarse basis functions at fine support
+ * points (Sec. 2, Eqs. pointwise, residual2; Sec. 3.2, Eq.
+ * tensor_product_evaluation) and restriction is its exact transpose.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Status: every call returns an int status (NNMG_OK = 0).  On failure the
+ *   library records a message readable with nnmg_last_error() (per host
+ *   thread) and leaves caller-owned outputs unspecified.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Device work is enqueued on it; calls that return host data
+ *   synchronise it.
+ * Ownership: the library copies every host input it needs; it owns all
+ *   hierarchy memory until nnmg_destroy.  Device vectors passed to compute
+ *   calls are owned by the caller and must stay valid until the stream has
+ *   finished the call's work.
+ * Precision: NNMG_F32 (float) or NNMG_F64 (double) for vector arguments
+ *   declared as void*.
+ * Vector layout: a vector on level l has n_nodes(l) * n_components rows; row
+ *   r = node * n_components + component; each row holds nrhs contiguous
+ *   values (right-hand side index fastest).  Element (node, comp, rhs) sits at
+ *   ((node * n_components + comp) * nrhs + rhs).  Entries at Dirichlet-
+ *   constrained DoFs are ignored on input and written as 0 on output.
+ * Node numbering: a local node of a cell is identified by the combination of
+ *   the cell's corner vertices that places it (integer weights
+ *   W_v = prod_d (b_d(v) ? m_d : k - m_d) for local multi-index m and corner
+ *   bits b(v)); nodes are numbered in order of first appearance, walking cells
+ *   in index order and each cell's (k+1)^d local nodes lexicographically
+ *   (x fastest).  Local node (m_0, m_1, m_2) sits at the Gauss-Lobatto point
+ *   (xi_{m_0}, xi_{m_1}, xi_{m_2}) of the reference cell [0,1]^d.
+ * Dirichlet set: all nodes on a boundary face (a face of exactly one cell)
+ *   whose corner vertices are all flagged in dirichlet_vertex.
+ * nrhs: 1 .. options.max_nrhs (<= 16).
+ */
+#ifndef NNMG_H
+#define NNMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nnmg_handle nnmg_handle;
+
+enum nnmg_status {
+  NNMG_OK = 0,
+  NNMG_INVALID_ARG = 1,     /* bad pointer, size, level index, nrhs or option   */
+  NNMG_BAD_MESH = 2,        /* non-positive Jacobian determinant at a quadrature point */
+  NNMG_POINT_NOT_FOUND = 3, /* a fine support point could not be located         */
+  NNMG_CHOLESKY_FAIL = 4,   /* coarsest matrix not positive definite             */
+  NNMG_OUT_OF_MEMORY = 5,   /* device or host allocation failed                  */
+  NNMG_CUDA_ERROR = 6,      /* a CUDA runtime call failed                         */
+  NNMG_NOT_CONVERGED = 7,   /* PCG reached maxit before rtol for some column      */
+  NNMG_BREAKDOWN = 8        /* PCG met p.Ap <= 0 or a non-finite scalar           */
+};
+
+enum nnmg_precision { NNMG_F32 = 0, NNMG_F64 = 1 };
+
+enum nnmg_mode {
+  NNMG_FP64_MG = 0,          /* V-cycle and CG in double precision                */
+  NNMG_FP32_MG_FP64_CG = 1   /* V-cycle in single precision inside a double CG (Sec. 4) */
+};
+
+/* One level of the hierarchy: a conforming quad (dim 2) or hex (dim 3) mesh.
+ * vertices: host, [n_vertices][dim] doubles.
+ * cells: host, [n_cells][2^dim] vertex indices; local corner v = b0 + 2 b1 + 4 b2
+ *   where b_d is the corner's offset bit in reference direction d.
+ * dirichlet_vertex: host, [n_vertices] flags (NULL = no Dirichlet boundary). */
+typedef struct {
+  int dim;
+  int64_t n_vertices;
+  const double* vertices;
+  int64_t n_cells;
+  const int32_t* cells;
+  const uint8_t* dirichlet_vertex;
+} nnmg_level_desc;
+
+/* Solver options (Sec. 4 solver settings; values in brackets are defaults).
+ * degree k [1] of Q_k; n_components [1] (1 = Poisson, 3 = linear elasticity in
+ * 3D, Sec. 4.4 Eq. linear_elasticity with Lame parameters lambda [1], mu [1]);
+ * cheb_degree [3] Chebyshev steps per smoothing; smoothing_range [20] and
+ * eig_safety [1.2] place the Chebyshev interval at
+ * [eig_safety*lam/smoothing_range, eig_safety*lam] for lam the Lanczos
+ * estimate after lanczos_steps [12] steps; max_nrhs [16] sizes work buffers. */
+typedef struct {
+  int degree;
+  int n_components;
+  double lambda;
+  double mu;
+  int cheb_degree;
+  double smoothing_range;
+  int lanczos_steps;
+  double eig_safety;
+  int max_nrhs;
+} nnmg_options;
+
+/* Fill *opt with the defaults above. */
+void nnmg_default_options(nnmg_options* opt);
+
+/* Build a hierarchy from n_levels >= 1 meshes ordered coarse -> fine (Sec. 2:
+ * level 1 coarsest, level L finest; here index 0 is the coarsest).  Setup
+ * (Sec. 3.1, 3.2): DoF numbering, geometry at quadrature points, support
+ * points, location of every free fine support point in the next coarser mesh
+ * (bounding-box buckets, Newton inversion of the Q1 cell map, first accepting
+ * cell by index, nearest-point projection onto [0,1]^d otherwise, Sec. 3.3
+ * Eq. closest_point), point-Jacobi diagonals, Lanczos eigenvalue estimates and
+ * the FP64 factorization of the coarsest operator.  Errors: INVALID_ARG,
+ * BAD_MESH, POINT_NOT_FOUND, CHOLESKY_FAIL, OUT_OF_MEMORY, CUDA_ERROR. */
+int nnmg_setup_hierarchy(const nnmg_level_desc* levels, int n_levels,
+                         const nnmg_options* opt, void* stream, nnmg_handle** out);
+
+/* Release all memory of a hierarchy (NULL is accepted). */
+int nnmg_destroy(nnmg_handle* h);
+
+/* Number of levels. */
+int nnmg_n_levels(const nnmg_handle* h);
+
+/* Sizes of one level: nodes, free (unconstrained) nodes and cells. */
+int nnmg_level_info(const nnmg_handle* h, int level, int64_t* n_nodes,
+                    int64_t* n_free_nodes, int64_t* n_cells);
+
+/* Device bytes held by the hierarchy (used to admit work against a budget). */
+size_t nnmg_hierarchy_bytes(const nnmg_handle* h);
+
+/* Device bytes the work buffers of one solve with nrhs columns will add. */
+size_t nnmg_solve_bytes(const nnmg_handle* h, int nrhs);
+
+/* Host copies of setup products of a level:
+ * support points x_i = F_K(xi_i) [n_nodes][dim] (Sec. 2 Eq. pointwise);
+ * constrained flags [n_nodes]; cell-to-node map [n_cells][(k+1)^d];
+ * physical quadrature points [n_cells][(k+1)^d][dim] (Gauss-Legendre, Sec. 4). */
+int nnmg_support_points(const nnmg_handle* h, int level, double* points);
+int nnmg_constrained_nodes(const nnmg_handle* h, int level, uint8_t* flags);
+int nnmg_cell_nodes(const nnmg_handle* h, int level, int32_t* cell_nodes);
+int nnmg_quadrature_points(const nnmg_handle* h, int level, double* xq);
+
+/* The located coarse cell and reference point of every free fine node of
+ * level fine_level >= 1 (Sec. 3.1), in increasing fine node order:
+ * cell [n_free_fine], xi [n_free_fine][dim] (clamped to [0,1]^d). */
+int nnmg_transfer_points(const nnmg_handle* h, int fine_level, int32_t* cell, double* xi);
+
+/* Lanczos estimate of lambda_max(D^-1 A_l) per level ([n_levels]; 0 on level 0). */
+int nnmg_eigen_estimates(const nnmg_handle* h, double* lam_max);
+
+/* Load vector b_(i,c) = sum_K sum_q w_q |det J| f_c(x_q) phi_i(xi_q) (Sec. 2,
+ * (f_l, v) = b(v)) written into column rhs_col of the device FP64 vector b
+ * [rows][nrhs].  f: host; if f_per_qp == 0 it holds n_components constants,
+ * else values [n_cells][(k+1)^d][n_components] at nnmg_quadrature_points.
+ * Constrained rows are written 0; other columns are left untouched. */
+int nnmg_load_vector(nnmg_handle* h, int level, const double* f, int f_per_qp,
+                     double* b, int nrhs, int rhs_col, void* stream);
+
+/* y = A_l x (Sec. 2, (A_l w, v) = a(w, v)), matrix-free with sum
+ * factorization (Sec. 3.2); x and y are device vectors of level `level` in
+ * `precision`, distinct, [rows][nrhs]. */
+int nnmg_apply_operator(nnmg_handle* h, int level, int precision, const void* x,
+                        void* y, int nrhs, void* stream);
+
+/* fine = P coarse (Sec. 2 transfer matrix P^(c,f); Sec. 3.2 evaluation at
+ * reference points).  fine_level >= 1; `coarse` lives on fine_level-1.
+ * Overwrites fine. */
+int nnmg_prolongate(nnmg_handle* h, int fine_level, int precision, const void* coarse,
+                    void* fine, int nrhs, void* stream);
+
+/* coarse = P^T fine (Sec. 2 Eq. residual2), a deterministic two-phase gather:
+ * bitwise reproducible for fixed inputs.  Overwrites coarse. */
+int nnmg_restrict(nnmg_handle* h, int fine_level, int precision, const void* fine,
+                  void* coarse, int nrhs, void* stream);
+
+/* One V-cycle (Algorithm 1) on the finest level from a zero guess: z ~ A_L^-1 r.
+ * Chebyshev-Jacobi pre- and post-smoothing, residual, restriction, recursion,
+ * prolongation; coarsest level solved directly in FP64. */
+int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
+                void* stream);
+
+/* PCG in FP64 from x0 = 0, preconditioned by one V-cycle per iteration
+ * (Sec. 4), per column until ||r_k||_2 <= rtol ||b||_2 (recursive residual).
+ * b, x: device FP64 [rows][nrhs]; iters_out, relres_out: host [nrhs] (may be
+ * NULL).  Returns NOT_CONVERGED (x still written) if a column misses rtol in
+ * maxit iterations, BREAKDOWN on p.Ap <= 0 or a non-finite scalar. */
+int nnmg_pcg_solve(nnmg_handle* h, int mode, const double* b, double* x, int nrhs,
+                   double rtol, int maxit, int* iters_out, double* relres_out,
+                   void* stream);
+
+/* As nnmg_pcg_solve with HOST b and x (pinned or pageable); the copies to and
+ * from the device are part of the call. */
+int nnmg_pcg_solve_host(nnmg_handle* h, int mode, const double* b_host, double* x_host,
+                        int nrhs, double rtol, int maxit, int* iters_out,
+                        double* relres_out, void* stream);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* nnmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NNMG_H */

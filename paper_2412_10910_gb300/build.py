@@ -1,0 +1,66 @@
+"""Build libnnmg.so in-tree: nvcc for sm_103a, translation units compiled in parallel."""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "libnnmg.so")
+BUILD = os.path.join(HERE, "_build")
+SOURCES = ["host_setup.cpp", "k_setup.cu", "k_operator.cu", "k_transfer.cu", "k_vector.cu",
+           "solver.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+         "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
+
+
+def nvcc():
+    exe = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(exe):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libnnmg")
+    return exe
+
+
+def _newer(src, obj):
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    deps = [src, os.path.join(CSRC, "nnmg_internal.h"),
+            os.path.join(HERE, "..", "include", "nnmg.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(verbose=False, force=False, extra=()):
+    os.makedirs(BUILD, exist_ok=True)
+    exe = nvcc()
+    jobs = []
+    objs = []
+    for src in SOURCES:
+        s = os.path.join(CSRC, src)
+        o = os.path.join(BUILD, src + ".o")
+        objs.append(o)
+        if force or _newer(s, o):
+            jobs.append([exe, *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if verbose or r.returncode:
+            sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
+        return r.returncode
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        rcs = list(ex.map(run, jobs))
+    if any(rcs):
+        raise RuntimeError("nvcc failed")
+    if jobs or not os.path.exists(OUT):
+        link = [exe, *ARCH, "-shared", "-o", OUT, *objs, "-lpthread"]
+        if run(link):
+            raise RuntimeError("link failed")
+    return OUT
+
+
+if __name__ == "__main__":
+    build(verbose="-v" in sys.argv, force="-f" in sys.argv)
+    print(OUT)

@@ -1,0 +1,425 @@
+// Matrix-free cell operator y = A_l x with sum factorization (Sec. 3.2,
+// Eq. tensor_product_evaluation for tensor point sets; Sec. 2 operator A_l).
+//
+// Per cell: gather the (k+1)^d nodal values, interpolate to the (k+1)^d
+// Gauss points (one 1D sweep per direction), take reference derivatives by
+// collocation on the Gauss points, apply the stored metric terms (Poisson:
+// G = |det J| w J^-1 J^-T; elasticity: sigma = lambda tr(eps) I + 2 mu eps,
+// Sec. 4.4), run the transposed sweeps and scatter-add into y.
+//
+// Thread mapping: a "unit" is one (cell, right-hand side) pair; a block holds
+// U units (right-hand side fastest, then cells) and (k+1)^(d-1) lines per
+// unit; thread t has unit t % U and line t / U, so a warp reads one node's
+// contiguous right-hand sides and neighbouring cells.  A thread keeps one
+// line of k+1 values in registers per sweep; sweeps along other directions go
+// through shared memory laid out [array][point][unit] (bank-conflict free).
+// Dirichlet nodes carry index -1: read as 0, never written.  y must be zero on
+// entry (scatter is atomic).
+#include "nnmg_internal.h"
+
+namespace nnmg {
+namespace {
+
+template <int N, typename T>
+__device__ __forceinline__ void apply(const T (&M)[kMaxN][kMaxN], const T* in, T* out) {
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    T s = 0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) s += M[q][l] * in[l];
+    out[q] = s;
+  }
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void apply_t(const T (&M)[kMaxN][kMaxN], const T* in, T* out) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    T s = 0;
+#pragma unroll
+    for (int q = 0; q < N; ++q) s += M[q][l] * in[q];
+    out[l] = s;
+  }
+}
+
+// Stress flux at one quadrature point for elasticity: g[c][a] = d u_c / d xi_a
+// in, F[c][a] out.  K = sqrt(|det J| w) J^-1, H = g K (scaled physical
+// gradient), sigma = lambda tr(H) I + mu (H + H^T), F = sigma K^T.
+template <typename T>
+__device__ __forceinline__ void elastic_flux(const T (&g)[3][3], const T (&K)[3][3], T lambda,
+                                             T mu, T (&F)[3][3]) {
+  T H[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) H[c][b] = g[c][0] * K[0][b] + g[c][1] * K[1][b] + g[c][2] * K[2][b];
+  const T tr = lambda * (H[0][0] + H[1][1] + H[2][2]);
+  T s[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) s[c][b] = mu * (H[c][b] + H[b][c]) + (c == b ? tr : T(0));
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[c][a] = s[c][0] * K[a][0] + s[c][1] * K[a][1] + s[c][2] * K[a][2];
+}
+
+template <int K, typename T, int NC>
+__global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __restrict__ metric,
+                            const T* __restrict__ x, T* __restrict__ y, int64_t n_cells, int nrhs,
+                            int U, Basis1D<T> B, T lambda, T mu) {
+  constexpr int N = K + 1, N2 = N * N, NQ = N2 * N;
+  constexpr int NM = NC == 1 ? 6 : 9;
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int unit = threadIdx.x % U;
+  const int line = threadIdx.x / U;
+  const int a = line % N, b = line / N;
+  const int rhs = unit % nrhs;
+  const int64_t cell = (int64_t)blockIdx.x * (U / nrhs) + unit / nrhs;
+  const bool act = cell < n_cells;
+  // shared arrays: for component c: A = 3c, Gx = 3c+1, Gy = 3c+2
+  auto S = [&](int arr, int idx) -> T& { return sm[(arr * NQ + idx) * U + unit]; };
+  const int rs = NC * nrhs;  // stride between node rows of one right-hand side
+
+  int dof[N];
+  // P0 + P1: gather the z-line (i=a, j=b) and interpolate along z in registers
+#pragma unroll
+  for (int l = 0; l < N; ++l) dof[l] = act ? cell_nodes[cell * NQ + a + N * b + N2 * l] : -1;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T u[N], v[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) u[l] = dof[l] >= 0 ? x[(int64_t)dof[l] * rs + c * nrhs + rhs] : T(0);
+    apply<N>(B.S, u, v);
+#pragma unroll
+    for (int q = 0; q < N; ++q) S(3 * c, a + N * b + N2 * q) = v[q];
+  }
+  __syncthreads();
+  // P2: interpolate along y, line (i=a, z=b)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T u[N], v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) u[j] = S(3 * c, a + N * j + N2 * b);
+    apply<N>(B.S, u, v);
+#pragma unroll
+    for (int q = 0; q < N; ++q) S(3 * c, a + N * q + N2 * b) = v[q];
+  }
+  __syncthreads();
+  // P3: interpolate along x and take the x derivative, line (y=a, z=b)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T u[N], v[N], g[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = S(3 * c, i + N * a + N2 * b);
+    apply<N>(B.S, u, v);
+    apply<N>(B.Dg, v, g);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      S(3 * c, q + N * a + N2 * b) = v[q];
+      S(3 * c + 1, q + N * a + N2 * b) = g[q];
+    }
+  }
+  __syncthreads();
+  // P4: y derivative, line (x=a, z=b)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T u[N], g[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) u[p] = S(3 * c, a + N * p + N2 * b);
+    apply<N>(B.Dg, u, g);
+#pragma unroll
+    for (int q = 0; q < N; ++q) S(3 * c + 2, a + N * q + N2 * b) = g[q];
+  }
+  __syncthreads();
+  // P5: z derivative, physics at the quadrature points of column (a, b),
+  // transposed z derivative
+  {
+    T gz[NC][N];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T u[N];
+#pragma unroll
+      for (int p = 0; p < N; ++p) u[p] = S(3 * c, a + N * b + N2 * p);
+      apply<N>(B.Dg, u, gz[c]);
+    }
+    const T* mc = metric + (act ? cell : 0) * NM * NQ;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      const int idx = a + N * b + N2 * q;
+      if constexpr (NC == 1) {
+        const T gx = S(1, idx), gy = S(2, idx), g3 = gz[0][q];
+        T G[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) G[m] = act ? mc[m * NQ + idx] : T(0);
+        S(1, idx) = G[0] * gx + G[1] * gy + G[2] * g3;
+        S(2, idx) = G[1] * gx + G[3] * gy + G[4] * g3;
+        gz[0][q] = G[2] * gx + G[4] * gy + G[5] * g3;
+      } else {
+        T g[3][3], Km[3][3], F[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          g[c][0] = S(3 * c + 1, idx);
+          g[c][1] = S(3 * c + 2, idx);
+          g[c][2] = gz[c][q];
+        }
+#pragma unroll
+        for (int m = 0; m < 9; ++m) Km[m / 3][m % 3] = act ? mc[m * NQ + idx] : T(0);
+        elastic_flux(g, Km, lambda, mu, F);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          S(3 * c + 1, idx) = F[c][0];
+          S(3 * c + 2, idx) = F[c][1];
+          gz[c][q] = F[c][2];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T w[N];
+      apply_t<N>(B.Dg, gz[c], w);
+#pragma unroll
+      for (int p = 0; p < N; ++p) S(3 * c, a + N * b + N2 * p) = w[p];
+    }
+  }
+  __syncthreads();
+  // P6: add the transposed y derivative, line (x=a, z=b)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T f[N], w[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) f[q] = S(3 * c + 2, a + N * q + N2 * b);
+    apply_t<N>(B.Dg, f, w);
+#pragma unroll
+    for (int p = 0; p < N; ++p) S(3 * c, a + N * p + N2 * b) += w[p];
+  }
+  __syncthreads();
+  // P7: add the transposed x derivative and integrate along x, line (y=a, z=b)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T f[N], w[N], o[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) f[q] = S(3 * c + 1, q + N * a + N2 * b);
+    apply_t<N>(B.Dg, f, w);
+#pragma unroll
+    for (int q = 0; q < N; ++q) w[q] += S(3 * c, q + N * a + N2 * b);
+    apply_t<N>(B.S, w, o);
+#pragma unroll
+    for (int i = 0; i < N; ++i) S(3 * c, i + N * a + N2 * b) = o[i];
+  }
+  __syncthreads();
+  // P8: integrate along y, line (x=a, z=b)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T f[N], o[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) f[q] = S(3 * c, a + N * q + N2 * b);
+    apply_t<N>(B.S, f, o);
+#pragma unroll
+    for (int j = 0; j < N; ++j) S(3 * c, a + N * j + N2 * b) = o[j];
+  }
+  __syncthreads();
+  // P9: integrate along z and scatter, column (a, b)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T f[N], o[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) f[q] = S(3 * c, a + N * b + N2 * q);
+    apply_t<N>(B.S, f, o);
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+      if (dof[l] >= 0) atomicAdd(&y[(int64_t)dof[l] * rs + c * nrhs + rhs], o[l]);
+  }
+}
+
+// 2D Poisson: one thread per x-column (i = a) or y-row.
+template <int K, typename T>
+__global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __restrict__ metric,
+                            const T* __restrict__ x, T* __restrict__ y, int64_t n_cells, int nrhs,
+                            int U, Basis1D<T> B) {
+  constexpr int N = K + 1, NQ = N * N;
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int unit = threadIdx.x % U;
+  const int a = threadIdx.x / U;
+  const int rhs = unit % nrhs;
+  const int64_t cell = (int64_t)blockIdx.x * (U / nrhs) + unit / nrhs;
+  const bool act = cell < n_cells;
+  auto S = [&](int arr, int idx) -> T& { return sm[(arr * NQ + idx) * U + unit]; };
+  int dof[N];
+  {
+    T u[N], v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      dof[j] = act ? cell_nodes[cell * NQ + a + N * j] : -1;
+      u[j] = dof[j] >= 0 ? x[(int64_t)dof[j] * nrhs + rhs] : T(0);
+    }
+    apply<N>(B.S, u, v);
+#pragma unroll
+    for (int q = 0; q < N; ++q) S(0, a + N * q) = v[q];
+  }
+  __syncthreads();
+  {  // x interpolation and derivative, row y = a
+    T u[N], v[N], g[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = S(0, i + N * a);
+    apply<N>(B.S, u, v);
+    apply<N>(B.Dg, v, g);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      S(0, q + N * a) = v[q];
+      S(1, q + N * a) = g[q];
+    }
+  }
+  __syncthreads();
+  {  // y derivative, metric, transposed y derivative, column x = a
+    T u[N], gy[N], w[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) u[p] = S(0, a + N * p);
+    apply<N>(B.Dg, u, gy);
+    const T* mc = metric + (act ? cell : 0) * 3 * NQ;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      const int idx = a + N * q;
+      const T gx = S(1, idx);
+      const T G0 = act ? mc[idx] : T(0), G1 = act ? mc[NQ + idx] : T(0),
+              G2 = act ? mc[2 * NQ + idx] : T(0);
+      S(1, idx) = G0 * gx + G1 * gy[q];
+      gy[q] = G1 * gx + G2 * gy[q];
+    }
+    apply_t<N>(B.Dg, gy, w);
+#pragma unroll
+    for (int p = 0; p < N; ++p) S(0, a + N * p) = w[p];
+  }
+  __syncthreads();
+  {  // transposed x derivative + x integration, row y = a
+    T f[N], w[N], o[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) f[q] = S(1, q + N * a);
+    apply_t<N>(B.Dg, f, w);
+#pragma unroll
+    for (int q = 0; q < N; ++q) w[q] += S(0, q + N * a);
+    apply_t<N>(B.S, w, o);
+#pragma unroll
+    for (int i = 0; i < N; ++i) S(0, i + N * a) = o[i];
+  }
+  __syncthreads();
+  {  // y integration and scatter, column x = a
+    T f[N], o[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) f[q] = S(0, a + N * q);
+    apply_t<N>(B.S, f, o);
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (dof[j] >= 0) atomicAdd(&y[(int64_t)dof[j] * nrhs + rhs], o[j]);
+  }
+}
+
+template <typename T>
+void pick_basis(int k, Basis1D<T>* b);
+template <>
+void pick_basis<double>(int k, Basis1D<double>* b) {
+  Basis1D<float> f;
+  make_basis(k, b, &f);
+}
+template <>
+void pick_basis<float>(int k, Basis1D<float>* b) {
+  Basis1D<double> d;
+  make_basis(k, &d, b);
+}
+
+struct OpConfig {
+  int U;
+  unsigned blocks;
+  int threads;
+  size_t smem;
+};
+
+inline OpConfig op_config(int lines, int nq, int arrays, size_t tsize, int64_t n_cells, int nrhs) {
+  int cpb = 256 / (lines * nrhs);
+  if (cpb < 1) cpb = 1;
+  OpConfig c;
+  c.U = cpb * nrhs;
+  c.threads = c.U * lines;
+  c.blocks = (unsigned)((n_cells + cpb - 1) / cpb);
+  c.smem = (size_t)arrays * nq * c.U * tsize;
+  return c;
+}
+
+template <int K, typename T, int NC>
+cudaError_t run3d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs, double lambda,
+                  double mu, cudaStream_t s) {
+  constexpr int N = K + 1;
+  Basis1D<T> B;
+  pick_basis<T>(K, &B);
+  OpConfig c = op_config(N * N, N * N * N, 3 * NC, sizeof(T), L.n_cells, nrhs);
+  auto kern = op3d_kernel<K, T, NC>;
+  static size_t smem_set = 48 * 1024;   // opt-in size already granted to this kernel
+  if (c.smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (e != cudaSuccess) return e;
+    smem_set = c.smem;
+  }
+  kern<<<c.blocks, c.threads, c.smem, s>>>(L.cell_nodes, metric, x, y, L.n_cells, nrhs, c.U, B,
+                                           (T)lambda, (T)mu);
+  return cudaGetLastError();
+}
+
+template <int K, typename T>
+cudaError_t run2d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs, cudaStream_t s) {
+  constexpr int N = K + 1;
+  Basis1D<T> B;
+  pick_basis<T>(K, &B);
+  OpConfig c = op_config(N, N * N, 2, sizeof(T), L.n_cells, nrhs);
+  op2d_kernel<K, T><<<c.blocks, c.threads, c.smem, s>>>(L.cell_nodes, metric, x, y, L.n_cells,
+                                                        nrhs, c.U, B);
+  return cudaGetLastError();
+}
+
+template <typename T>
+const T* metric_of(const DevLevel& L);
+template <>
+const double* metric_of<double>(const DevLevel& L) { return L.metric64; }
+template <>
+const float* metric_of<float>(const DevLevel& L) { return L.metric32; }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, double lambda,
+                            double mu, cudaStream_t s) {
+  if (L.n_cells == 0) return cudaSuccess;
+  const T* m = metric_of<T>(L);
+  if (L.dim == 2) {
+    switch (L.k) {
+      case 1: return run2d<1, T>(L, m, x, y, nrhs, s);
+      case 2: return run2d<2, T>(L, m, x, y, nrhs, s);
+      case 3: return run2d<3, T>(L, m, x, y, nrhs, s);
+      case 4: return run2d<4, T>(L, m, x, y, nrhs, s);
+    }
+  } else if (L.ncomp == 1) {
+    switch (L.k) {
+      case 1: return run3d<1, T, 1>(L, m, x, y, nrhs, lambda, mu, s);
+      case 2: return run3d<2, T, 1>(L, m, x, y, nrhs, lambda, mu, s);
+      case 3: return run3d<3, T, 1>(L, m, x, y, nrhs, lambda, mu, s);
+      case 4: return run3d<4, T, 1>(L, m, x, y, nrhs, lambda, mu, s);
+    }
+  } else {
+    switch (L.k) {
+      case 1: return run3d<1, T, 3>(L, m, x, y, nrhs, lambda, mu, s);
+      case 2: return run3d<2, T, 3>(L, m, x, y, nrhs, lambda, mu, s);
+      case 3: return run3d<3, T, 3>(L, m, x, y, nrhs, lambda, mu, s);
+      case 4: return run3d<4, T, 3>(L, m, x, y, nrhs, lambda, mu, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_operator<float>(const DevLevel&, const float*, float*, int, double,
+                                            double, cudaStream_t);
+template cudaError_t launch_operator<double>(const DevLevel&, const double*, double*, int, double,
+                                             double, cudaStream_t);
+
+}  // namespace nnmg

@@ -1,0 +1,284 @@
+// Non-nested transfer kernels and the coarsest-level solve.
+//
+// Prolongation x_f += P x_c (Sec. 2, P[i,j] = phi^{l-1}_j(x_i); Sec. 3.2,
+// Eqs. local_evaluation, tensor_product_evaluation): one block per coarse cell
+// stages the cell's (k+1)^d coarse values for all channels in shared memory;
+// each (fine point, channel) pair tabulates the 1D Lagrange bases at its
+// reference point and contracts them direction by direction.  Every fine point
+// belongs to exactly one coarse cell, so its output is written once (no
+// atomics).
+//
+// Restriction r_c = P^T r_f (Sec. 2, Eq. residual2) in two deterministic
+// phases: (1) per coarse cell, each (local node, channel) pair sums
+// phi_j(xi_p) r_f(p) over the cell's fine points in their stored order into a
+// cell-local buffer; (2) per coarse node, the buffer entries of the cells that
+// share it are summed in ascending (cell, local) order.  No atomics: results
+// are bitwise reproducible.
+#include "nnmg_internal.h"
+
+namespace nnmg {
+namespace {
+
+template <int N, typename T>
+__device__ __forceinline__ void lagrange1d(const Basis1D<T>& B, T xi, T* L) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    T v = B.gl_scale[l];
+#pragma unroll
+    for (int m = 0; m < N; ++m)
+      if (m != l) v *= xi - B.gl[m];
+    L[l] = v;
+  }
+}
+
+template <int D, int K, typename T>
+__global__ void prolong_kernel(const int32_t* __restrict__ coarse_cell_nodes,
+                               const T* __restrict__ xc, T* __restrict__ xf,
+                               const int32_t* __restrict__ cell_pt_start,
+                               const int32_t* __restrict__ pt_node, const T* __restrict__ pt_xi,
+                               int nch, Basis1D<T> B) {
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  extern __shared__ unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);  // [NL][nch]
+  const int64_t c = blockIdx.x;
+  for (int e = threadIdx.x; e < NL * nch; e += blockDim.x) {
+    const int j = e / nch, ch = e - j * nch;
+    const int node = coarse_cell_nodes[c * NL + j];
+    su[e] = node >= 0 ? xc[(int64_t)node * nch + ch] : T(0);
+  }
+  __syncthreads();
+  const int p0 = cell_pt_start[c], p1 = cell_pt_start[c + 1];
+  for (int e = threadIdx.x; e < (p1 - p0) * nch; e += blockDim.x) {
+    const int pl = e / nch, ch = e - pl * nch;
+    const int p = p0 + pl;
+    T L[D][N];
+#pragma unroll
+    for (int d = 0; d < D; ++d) lagrange1d<N, T>(B, pt_xi[(int64_t)p * D + d], L[d]);
+    T val = 0;
+    if constexpr (D == 2) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        T s = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) s += L[0][i] * su[(i + N * j) * nch + ch];
+        val += L[1][j] * s;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        T s1 = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          T s0 = 0;
+#pragma unroll
+          for (int i = 0; i < N; ++i) s0 += L[0][i] * su[(i + N * j + N * N * l) * nch + ch];
+          s1 += L[1][j] * s0;
+        }
+        val += L[2][l] * s1;
+      }
+    }
+    T* o = xf + (int64_t)pt_node[p] * nch + ch;
+    *o += val;
+  }
+}
+
+constexpr int kChunk = 64;
+
+template <int D, int K, typename T>
+__global__ void restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
+                                 const int32_t* __restrict__ cell_pt_start,
+                                 const int32_t* __restrict__ pt_node, const T* __restrict__ pt_xi,
+                                 int nch, Basis1D<T> B) {
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  __shared__ T sL[kChunk][D][N];
+  extern __shared__ unsigned char smem_raw[];
+  T* sr = reinterpret_cast<T*>(smem_raw);  // [kChunk][nch]
+  const int64_t c = blockIdx.x;
+  const int e = blockIdx.y * blockDim.x + threadIdx.x;
+  const bool valid = e < NL * nch;
+  const int j = valid ? e / nch : 0;
+  const int ch = valid ? e - j * nch : 0;
+  const int mi[3] = {j % N, (j / N) % N, j / (N * N)};
+  const int p0 = cell_pt_start[c], p1 = cell_pt_start[c + 1];
+  T acc = 0;
+  for (int q0 = p0; q0 < p1; q0 += kChunk) {
+    const int np = min(kChunk, p1 - q0);
+    for (int t = threadIdx.x; t < np * D; t += blockDim.x) {
+      const int pp = t / D, d = t - pp * D;
+      lagrange1d<N, T>(B, pt_xi[(int64_t)(q0 + pp) * D + d], sL[pp][d]);
+    }
+    for (int t = threadIdx.x; t < np * nch; t += blockDim.x) {
+      const int pp = t / nch, cc = t - pp * nch;
+      sr[t] = rf[(int64_t)pt_node[q0 + pp] * nch + cc];
+    }
+    __syncthreads();
+    if (valid) {
+      for (int pp = 0; pp < np; ++pp) {
+        T w = sL[pp][0][mi[0]] * sL[pp][1][mi[1]];
+        if constexpr (D == 3) w *= sL[pp][2][mi[2]];
+        acc += w * sr[pp * nch + ch];
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) buf[(c * NL + j) * nch + ch] = acc;
+}
+
+template <typename T>
+__global__ void restrict2_kernel(const T* __restrict__ buf, const int32_t* __restrict__ gstart,
+                                 const int32_t* __restrict__ gpos, T* __restrict__ rc,
+                                 int64_t n_nodes, int nch) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_nodes * nch) return;
+  const int64_t node = e / nch;
+  const int ch = (int)(e - node * nch);
+  T s = 0;
+  for (int k = gstart[node]; k < gstart[node + 1]; ++k) s += buf[(int64_t)gpos[k] * nch + ch];
+  rc[e] = s;
+}
+
+// z[free_i] = sum_j Ainv[i][j] r[free_j], one warp per free row, FP64 accumulation.
+template <typename TI, typename TO>
+__global__ void coarse_solve_kernel(const double* __restrict__ Ainv, const int32_t* __restrict__ rows,
+                                    int n, const TI* __restrict__ r, TO* __restrict__ z, int nrhs) {
+  const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  double acc[kMaxRhs];
+#pragma unroll
+  for (int q = 0; q < kMaxRhs; ++q) acc[q] = 0.0;
+  const double* arow = Ainv + (int64_t)w * n;
+  for (int j = lane; j < n; j += 32) {
+    const double a = arow[j];
+    const int64_t rj = (int64_t)rows[j] * nrhs;
+#pragma unroll
+    for (int q = 0; q < kMaxRhs; ++q)
+      if (q < nrhs) acc[q] += a * (double)r[rj + q];
+  }
+#pragma unroll
+  for (int q = 0; q < kMaxRhs; ++q) {
+    if (q < nrhs) {
+      double v = acc[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[q] = v;
+    }
+  }
+  if (lane == 0) {
+    const int64_t ri = (int64_t)rows[w] * nrhs;
+    for (int q = 0; q < nrhs; ++q) z[ri + q] = (TO)acc[q];
+  }
+}
+
+template <typename T>
+void basis_of(int k, Basis1D<T>* b);
+template <>
+void basis_of<double>(int k, Basis1D<double>* b) {
+  Basis1D<float> f;
+  make_basis(k, b, &f);
+}
+template <>
+void basis_of<float>(int k, Basis1D<float>* b) {
+  Basis1D<double> d;
+  make_basis(k, &d, b);
+}
+
+template <typename T>
+const T* xi_of(const DevLevel& L);
+template <>
+const double* xi_of<double>(const DevLevel& L) { return L.pt_xi64; }
+template <>
+const float* xi_of<float>(const DevLevel& L) { return L.pt_xi32; }
+
+template <int D, int K, typename T>
+cudaError_t prolong_dk(const DevLevel& f, const DevLevel& c, const T* xc, T* xf, int nch,
+                       cudaStream_t s) {
+  Basis1D<T> B;
+  basis_of<T>(K, &B);
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  const size_t smem = (size_t)NL * nch * sizeof(T);
+  auto kern = prolong_kernel<D, K, T>;
+  static size_t smem_set = 48 * 1024;
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
+  kern<<<(unsigned)c.n_cells, 128, smem, s>>>(c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node,
+                                              xi_of<T>(f), nch, B);
+  return cudaGetLastError();
+}
+
+template <int D, int K, typename T>
+cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* rc, T* scratch,
+                        int nch, cudaStream_t s) {
+  Basis1D<T> B;
+  basis_of<T>(K, &B);
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  const size_t smem = (size_t)kChunk * nch * sizeof(T);
+  dim3 grid((unsigned)c.n_cells, (unsigned)((NL * nch + 255) / 256));
+  restrict1_kernel<D, K, T><<<grid, 256, smem, s>>>(rf, scratch, f.cell_pt_start, f.pt_node,
+                                                    xi_of<T>(f), nch, B);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t n = c.n_nodes * nch;
+  restrict2_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(scratch, c.gather_start,
+                                                                  c.gather_pos, rc, c.n_nodes, nch);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_prolongate_add(const DevLevel& fine, const DevLevel& coarse, const T* xc,
+                                  T* xf, int nrhs, cudaStream_t s) {
+  if (coarse.n_cells == 0) return cudaSuccess;
+  const int nch = fine.ncomp * nrhs;
+#define NNMG_P(D, K) \
+  if (fine.dim == D && fine.k == K) return prolong_dk<D, K, T>(fine, coarse, xc, xf, nch, s);
+  NNMG_P(2, 1) NNMG_P(2, 2) NNMG_P(2, 3) NNMG_P(2, 4)
+  NNMG_P(3, 1) NNMG_P(3, 2) NNMG_P(3, 3) NNMG_P(3, 4)
+#undef NNMG_P
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const T* rf, T* rc,
+                            T* scratch, int nrhs, cudaStream_t s) {
+  if (coarse.n_cells == 0) return cudaSuccess;
+  const int nch = fine.ncomp * nrhs;
+#define NNMG_R(D, K) \
+  if (fine.dim == D && fine.k == K) return restrict_dk<D, K, T>(fine, coarse, rf, rc, scratch, nch, s);
+  NNMG_R(2, 1) NNMG_R(2, 2) NNMG_R(2, 3) NNMG_R(2, 4)
+  NNMG_R(3, 1) NNMG_R(3, 2) NNMG_R(3, 3) NNMG_R(3, 4)
+#undef NNMG_R
+  return cudaErrorInvalidValue;
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs, cudaStream_t s) {
+  if (L.n_free_rows == 0) return cudaSuccess;
+  const int64_t threads = (int64_t)L.n_free_rows * 32;
+  coarse_solve_kernel<TI, TO><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      L.coarse_inv, L.free_rows, L.n_free_rows, r, z, nrhs);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_prolongate_add<float>(const DevLevel&, const DevLevel&, const float*,
+                                                  float*, int, cudaStream_t);
+template cudaError_t launch_prolongate_add<double>(const DevLevel&, const DevLevel&, const double*,
+                                                   double*, int, cudaStream_t);
+template cudaError_t launch_restrict<float>(const DevLevel&, const DevLevel&, const float*, float*,
+                                            float*, int, cudaStream_t);
+template cudaError_t launch_restrict<double>(const DevLevel&, const DevLevel&, const double*,
+                                             double*, double*, int, cudaStream_t);
+template cudaError_t launch_coarse_solve<float, float>(const DevLevel&, const float*, float*, int,
+                                                      cudaStream_t);
+template cudaError_t launch_coarse_solve<double, double>(const DevLevel&, const double*, double*,
+                                                         int, cudaStream_t);
+
+}  // namespace nnmg

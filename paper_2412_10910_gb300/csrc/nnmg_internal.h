@@ -1,0 +1,203 @@
+// Internal declarations of the GB300 non-nested multigrid library.
+//
+// Data layout in device memory (one hierarchy):
+//   per level: cell_nodes [n_cells][(k+1)^d] int32 with -1 at Dirichlet nodes;
+//   metric terms per quadrature point, [n_cells][n_metric][(k+1)^d] (component
+//   outer, quadrature point inner, so neighbouring threads read neighbouring
+//   words) in FP64 and FP32; inverse Jacobi diagonals per row in FP64 and FP32;
+//   for a level l >= 1 the located fine points sorted by coarse cell
+//   (fine node, reference point) with a CSR start per coarse cell; for a level
+//   used as coarse level the restriction gather list node -> (cell*nloc+local).
+//   Vectors are [rows][nrhs] with rows = n_nodes * n_components.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nnmg.h"
+
+namespace nnmg {
+
+constexpr int kMaxDegree = 4;
+constexpr int kMaxN = kMaxDegree + 1;
+constexpr int kMaxRhs = 16;
+
+// 1D tables for one degree k (n = k+1 points), passed to kernels by value.
+//   S[q][l]  = L_l(g_q): Gauss-Lobatto Lagrange basis at Gauss point q
+//   Dg[q][p] = derivative at g_q of the Lagrange basis on the Gauss points
+//   DS[q][l] = L_l'(g_q)
+//   gl[l]    = Gauss-Lobatto node l on [0,1]; gl_scale[l] = 1/prod_{m!=l}(gl_l-gl_m)
+//   gx[q], gw[q] = Gauss-Legendre points and weights on [0,1]
+template <typename T>
+struct Basis1D {
+  T S[kMaxN][kMaxN];
+  T Dg[kMaxN][kMaxN];
+  T DS[kMaxN][kMaxN];
+  T gl[kMaxN];
+  T gl_scale[kMaxN];
+  T gx[kMaxN];
+  T gw[kMaxN];
+};
+
+// Host side: tables in double for degree k (Newton on Legendre polynomials).
+void make_basis(int k, Basis1D<double>* b64, Basis1D<float>* b32);
+
+// Error record set by every entry point.
+void set_error(const std::string& msg);
+const char* get_error();
+
+#define NNMG_CUDA(call)                                                         \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      ::nnmg::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));    \
+      return NNMG_CUDA_ERROR;                                                   \
+    }                                                                           \
+  } while (0)
+
+// ---------------------------------------------------------------- host mesh
+struct HostNumbering {
+  std::vector<int32_t> cell_nodes;   // [nc][nloc]
+  int64_t n_nodes = 0;
+  std::vector<int32_t> owner_cell;   // [n_nodes]
+  std::vector<int32_t> owner_local;  // [n_nodes]
+  std::vector<uint8_t> constrained;  // [n_nodes]
+};
+int number_nodes(const int32_t* cells, int64_t nc, int64_t nv, int dim, int k,
+                 const uint8_t* dirichlet_vertex, HostNumbering* out);
+
+struct BucketGeom {            // plain data, passed to the location kernel
+  double lo[3], inv_w[3];
+  int nb[3];
+  double eps;                  // bounding-box widening
+};
+struct BucketGrid {
+  BucketGeom geo;
+  std::vector<int32_t> start;  // [n_buckets+1]
+  std::vector<int32_t> cells;  // ascending within a bucket
+};
+void build_buckets(const double* vertices, const int32_t* cells, int64_t nc, int dim,
+                   BucketGrid* g, std::vector<double>* aabb);
+
+// Dense SPD factorisation and inverse on the host (FP64): inv = A^-1.
+// Returns false if a pivot is not positive.
+bool dense_spd_inverse(std::vector<double>& a, int n, std::vector<double>* inv);
+
+// ------------------------------------------------------------ device levels
+struct DevLevel {
+  int dim = 0, k = 0, n1 = 0, nloc = 0, ncomp = 1, nmetric = 0;
+  int64_t n_vertices = 0, n_cells = 0, n_nodes = 0, n_free_nodes = 0, rows = 0;
+  HostNumbering num;                 // host numbering (kept for queries)
+  std::vector<double> h_vertices;
+  std::vector<int32_t> h_cells;
+  double* vertices = nullptr;        // [nv][dim]
+  int32_t* cells = nullptr;          // [nc][2^dim]
+  int32_t* cell_nodes = nullptr;     // [nc][nloc], -1 = constrained
+  int32_t* owner_cell = nullptr;     // [n_nodes]
+  int32_t* owner_local = nullptr;    // [n_nodes]
+  double* metric64 = nullptr;        // [nc][nmetric][nloc]
+  float* metric32 = nullptr;
+  double* diag64 = nullptr;          // [rows] (0 at constrained rows)
+  double* dinv64 = nullptr;          // [rows] (0 at constrained rows)
+  float* dinv32 = nullptr;
+  uint8_t* row_free = nullptr;       // [rows]
+  double* points = nullptr;          // [n_nodes][dim]
+  double lam_max = 0.0;
+  double cheb_a = 0.0, cheb_b = 0.0;
+  // transfer from the next coarser level (this level is the fine one), l >= 1
+  int64_t n_pts = 0;
+  int32_t* pt_node = nullptr;        // [n_pts] fine node, sorted by coarse cell
+  double* pt_xi64 = nullptr;         // [n_pts][dim]
+  float* pt_xi32 = nullptr;
+  int32_t* cell_pt_start = nullptr;  // [n_cells(coarse)+1]
+  std::vector<int32_t> h_loc_cell;   // by increasing free fine node
+  std::vector<double> h_loc_xi;
+  // restriction gather lists of this level as a coarse level
+  int32_t* gather_start = nullptr;   // [n_nodes+1]
+  int32_t* gather_pos = nullptr;     // [..] cell*nloc + local, ascending
+  // coarsest level direct solve
+  int n_free_rows = 0;
+  int32_t* free_rows = nullptr;      // [n_free_rows]
+  double* coarse_inv = nullptr;      // [n_free_rows][n_free_rows]
+};
+
+// ---------------------------------------------------------------- kernels
+// Launchers return cudaGetLastError() of the launch.
+cudaError_t launch_metric(const DevLevel& L, int* d_err, cudaStream_t s);
+cudaError_t launch_support_points(const DevLevel& L, cudaStream_t s);
+cudaError_t launch_diag(const DevLevel& L, double lambda, double mu, cudaStream_t s);
+cudaError_t launch_quad_points(const DevLevel& L, double* xq, cudaStream_t s);
+cudaError_t launch_load_vector(const DevLevel& L, const double* f, int f_per_qp, double* b,
+                               int nrhs, int col, cudaStream_t s);
+cudaError_t launch_locate(const DevLevel& coarse, const double* points, const int32_t* pt_nodes,
+                          int64_t n_pts, const int32_t* bucket_start, const int32_t* bucket_cells,
+                          const double* aabb, const BucketGeom& g, int32_t* out_cell,
+                          double* out_xi, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, double lambda,
+                            double mu, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolongate_add(const DevLevel& fine, const DevLevel& coarse, const T* xc,
+                                  T* xf, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const T* rf, T* rc,
+                            T* scratch, int nrhs, cudaStream_t s);
+template <typename TI, typename TO>
+cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs, cudaStream_t s);
+
+// vector kernels, rows x nrhs
+template <typename T>
+cudaError_t launch_cheb_init(const T* f, const T* dinv, T* d, T* x, double c, int64_t rows,
+                             int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cheb_step(const T* f, T* t, const T* dinv, T* d, T* x, double cd, double cr,
+                             int64_t rows, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(const T* f, T* t, T* r, int64_t rows, int nrhs, cudaStream_t s);
+template <typename TI, typename TO>
+cudaError_t launch_cast(const TI* a, TO* b, int64_t n, cudaStream_t s);
+
+// PCG (FP64) helpers.  Per-column scalars live in a device struct.
+struct PcgScalars {
+  double rho[kMaxRhs];
+  double alpha[kMaxRhs];
+  double beta[kMaxRhs];
+  double bnorm[kMaxRhs];
+  double rnorm[kMaxRhs];
+  int active[kMaxRhs];
+  int iters[kMaxRhs];
+  int first;
+  int any_active;
+  int breakdown;
+  double rtol;
+};
+constexpr int kDotBlocks = 152 * 4;
+constexpr int kDotThreads = 256;
+template <typename TB>
+cudaError_t launch_dot_partial(const double* a, const TB* b, double* partial, int64_t rows,
+                               int nrhs, cudaStream_t s);
+cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r, double* x,
+                            double* p, double* partial, int64_t rows, int nrhs, cudaStream_t s);
+cudaError_t launch_pcg_start(PcgScalars* sc, const double* partial, int nrhs, double rtol,
+                             cudaStream_t s);
+template <typename TZ>
+cudaError_t launch_pcg_beta_p(PcgScalars* sc, const double* partial, const TZ* z, double* p,
+                              int64_t rows, int nrhs, cudaStream_t s);
+cudaError_t launch_pcg_alpha(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s);
+cudaError_t launch_pcg_update(const PcgScalars* sc, const double* p, double* q, double* x,
+                              double* r, double* partial, int64_t rows, int nrhs, cudaStream_t s);
+cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s);
+// Lanczos helper: w = dinv .* u - beta * vprev  (nrhs = 1)
+cudaError_t launch_axpby_dinv(const double* u, const double* dinv, const double* vprev,
+                              double beta, double* w, int64_t rows, cudaStream_t s);
+cudaError_t launch_dot_weighted(const double* a, const double* b, const double* wgt,
+                                double* partial, int64_t rows, cudaStream_t s);
+cudaError_t launch_axpy(double a, const double* x, double* y, double scale_y, int64_t rows,
+                        cudaStream_t s);
+
+}  // namespace nnmg

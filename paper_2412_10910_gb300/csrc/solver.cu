@@ -1,0 +1,997 @@
+// Hierarchy setup, V-cycle (Sec. 2 Algorithm 1), PCG (Sec. 4) and the C
+// entry points declared in include/nnmg.h.
+//
+// The V-cycle and each PCG iteration are enqueued as a fixed sequence of
+// kernels on internal buffers; after a first eager run they are captured once
+// per (precision or mode, nrhs) into a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <new>
+#include <tuple>
+
+#include "nnmg_internal.h"
+
+using namespace nnmg;
+
+namespace nnmg {
+cudaError_t launch_finalize_diag(const double* diag, const uint8_t* row_free, double* dinv64,
+                                 float* dinv32, int64_t rows, cudaStream_t s);
+}
+
+template <typename T>
+struct WorkSet {
+  bool ready = false;
+  std::vector<T*> f, x, t, d, scratch;
+};
+
+struct nnmg_handle {
+  nnmg_options opt;
+  std::vector<DevLevel> lv;
+  cudaStream_t cap = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  size_t work_bytes = 0;
+  WorkSet<float> w32;
+  WorkSet<double> w64;
+  bool pcg_ready = false;
+  double *px = nullptr, *pr = nullptr, *pp = nullptr, *pq = nullptr, *pb = nullptr;
+  double* partial = nullptr;
+  PcgScalars* sc = nullptr;
+  PcgScalars* h_sc = nullptr;
+  std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (kind, prec/mode, nrhs)
+  std::map<std::tuple<int, int, int>, int> runs;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(nnmg_handle* h, T** p, size_t count, bool work = false) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back((void*)*p);
+  if (work)
+    h->work_bytes += count * sizeof(T);
+  else
+    h->bytes += count * sizeof(T);
+  return cudaSuccess;
+}
+
+#define CK(...)                                                                    \
+  do {                                                                             \
+    cudaError_t e_ = (__VA_ARGS__);                                                \
+    if (e_ != cudaSuccess) {                                                       \
+      set_error(std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));        \
+      return e_ == cudaErrorMemoryAllocation ? NNMG_OUT_OF_MEMORY : NNMG_CUDA_ERROR; \
+    }                                                                              \
+  } while (0)
+
+template <typename T>
+const T* dinv_of(const DevLevel& L);
+template <>
+const float* dinv_of<float>(const DevLevel& L) { return L.dinv32; }
+template <>
+const double* dinv_of<double>(const DevLevel& L) { return L.dinv64; }
+
+template <typename T>
+WorkSet<T>& work_of(nnmg_handle* h);
+template <>
+WorkSet<float>& work_of<float>(nnmg_handle* h) { return h->w32; }
+template <>
+WorkSet<double>& work_of<double>(nnmg_handle* h) { return h->w64; }
+
+template <typename T>
+int ensure_work(nnmg_handle* h) {
+  WorkSet<T>& W = work_of<T>(h);
+  if (W.ready) return NNMG_OK;
+  const int n = (int)h->lv.size();
+  const int mr = h->opt.max_nrhs;
+  W.f.assign(n, nullptr);
+  W.x.assign(n, nullptr);
+  W.t.assign(n, nullptr);
+  W.d.assign(n, nullptr);
+  W.scratch.assign(n, nullptr);
+  for (int l = 0; l < n; ++l) {
+    const DevLevel& L = h->lv[l];
+    const size_t m = (size_t)L.rows * mr;
+    CK(dalloc(h, &W.f[l], m, true));
+    CK(dalloc(h, &W.x[l], m, true));
+    CK(cudaMemset(W.f[l], 0, m * sizeof(T)));
+    CK(cudaMemset(W.x[l], 0, m * sizeof(T)));
+    if (l >= 1) {
+      CK(dalloc(h, &W.t[l], m, true));
+      CK(dalloc(h, &W.d[l], m, true));
+      CK(cudaMemset(W.t[l], 0, m * sizeof(T)));
+      CK(cudaMemset(W.d[l], 0, m * sizeof(T)));
+      const DevLevel& C = h->lv[l - 1];
+      const size_t sm = (size_t)C.n_cells * C.nloc * L.ncomp * mr;
+      CK(dalloc(h, &W.scratch[l], sm, true));
+    }
+  }
+  W.ready = true;
+  return NNMG_OK;
+}
+
+int ensure_pcg(nnmg_handle* h) {
+  if (h->pcg_ready) return NNMG_OK;
+  const DevLevel& L = h->lv.back();
+  const size_t m = (size_t)L.rows * h->opt.max_nrhs;
+  CK(dalloc(h, &h->px, m, true));
+  CK(dalloc(h, &h->pr, m, true));
+  CK(dalloc(h, &h->pp, m, true));
+  CK(dalloc(h, &h->pq, m, true));
+  CK(dalloc(h, &h->pb, m, true));
+  CK(cudaMemset(h->pq, 0, m * sizeof(double)));
+  CK(dalloc(h, &h->partial, (size_t)kDotBlocks * kMaxRhs, true));
+  CK(dalloc(h, &h->sc, 1, true));
+  CK(cudaMallocHost((void**)&h->h_sc, sizeof(PcgScalars)));
+  h->pcg_ready = true;
+  return NNMG_OK;
+}
+
+// ------------------------------------------------------------------ V-cycle
+// Algorithm 1 with Chebyshev-Jacobi smoothing (Sec. 4): pre-smoothing from a
+// zero guess (m steps, m-1 operator applications), residual, restriction
+// r_{l-1} = P^T r_l, recursion, prolongation x_l += P delta_{l-1},
+// post-smoothing continuing from x_l (m steps), FP64 direct solve on level 0.
+template <typename T>
+cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_t s) {
+  WorkSet<T>& W = work_of<T>(h);
+  const int top = (int)h->lv.size() - 1;
+  const int m = h->opt.cheb_degree;
+  const double lam = h->opt.lambda, mu = h->opt.mu;
+  cudaError_t e;
+#define RET(...)                        \
+  do {                                  \
+    e = (__VA_ARGS__);                  \
+    if (e != cudaSuccess) return e;     \
+  } while (0)
+  for (int l = top; l >= 1; --l) {
+    const DevLevel& L = h->lv[l];
+    const T* f = l == top ? f_top : W.f[l];
+    T *x = W.x[l], *t = W.t[l], *d = W.d[l];
+    const T* dinv = dinv_of<T>(L);
+    const double a = L.cheb_a, b = L.cheb_b;
+    const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
+    RET(launch_cheb_init<T>(f, dinv, d, x, 1.0 / theta, L.rows, nrhs, s));
+    double rho = 1.0 / sigma;
+    for (int j = 1; j < m; ++j) {
+      RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s));
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      RET(launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
+      rho = rn;
+    }
+    RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s));
+    RET(launch_residual<T>(f, t, d, L.rows, nrhs, s));
+    RET(launch_restrict<T>(L, h->lv[l - 1], d, W.f[l - 1], W.scratch[l], nrhs, s));
+  }
+  {
+    const T* f0 = top == 0 ? f_top : W.f[0];
+    RET(launch_coarse_solve<T, T>(h->lv[0], f0, W.x[0], nrhs, s));
+  }
+  for (int l = 1; l <= top; ++l) {
+    const DevLevel& L = h->lv[l];
+    const T* f = l == top ? f_top : W.f[l];
+    T *x = W.x[l], *t = W.t[l], *d = W.d[l];
+    const T* dinv = dinv_of<T>(L);
+    RET(launch_prolongate_add<T>(L, h->lv[l - 1], W.x[l - 1], x, nrhs, s));
+    const double a = L.cheb_a, b = L.cheb_b;
+    const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s));
+    RET(launch_cheb_step<T>(f, t, dinv, d, x, 0.0, 1.0 / theta, L.rows, nrhs, s));
+    for (int j = 1; j < m; ++j) {
+      RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s));
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      RET(launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
+      rho = rn;
+    }
+  }
+#undef RET
+  return cudaSuccess;
+}
+
+// One PCG iteration: z = M r, beta, p = z + beta p, q = A p, alpha, x, r updates,
+// convergence check.  All per-column scalars stay on the device.
+cudaError_t enqueue_pcg_iter(nnmg_handle* h, int mode, int nrhs, cudaStream_t s) {
+  const DevLevel& L = h->lv.back();
+  const int top = (int)h->lv.size() - 1;
+  const int64_t rows = L.rows;
+  cudaError_t e;
+  if (mode == NNMG_FP32_MG_FP64_CG) {
+    e = launch_cast<double, float>(h->pr, h->w32.f[top], rows * nrhs, s);
+    if (e != cudaSuccess) return e;
+    e = enqueue_vcycle<float>(h, h->w32.f[top], nrhs, s);
+    if (e != cudaSuccess) return e;
+    const float* z = h->w32.x[top];
+    if ((e = launch_dot_partial<float>(h->pr, z, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
+    if ((e = launch_pcg_beta_p<float>(h->sc, h->partial, z, h->pp, rows, nrhs, s)) != cudaSuccess) return e;
+  } else {
+    e = enqueue_vcycle<double>(h, h->pr, nrhs, s);
+    if (e != cudaSuccess) return e;
+    const double* z = h->w64.x[top];
+    if ((e = launch_dot_partial<double>(h->pr, z, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
+    if ((e = launch_pcg_beta_p<double>(h->sc, h->partial, z, h->pp, rows, nrhs, s)) != cudaSuccess) return e;
+  }
+  if ((e = launch_operator<double>(L, h->pp, h->pq, nrhs, h->opt.lambda, h->opt.mu, s)) != cudaSuccess) return e;
+  if ((e = launch_dot_partial<double>(h->pp, h->pq, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
+  if ((e = launch_pcg_alpha(h->sc, h->partial, nrhs, s)) != cudaSuccess) return e;
+  if ((e = launch_pcg_update(h->sc, h->pp, h->pq, h->px, h->pr, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
+  return launch_pcg_check(h->sc, h->partial, nrhs, s);
+}
+
+// Run `body` on stream s: eagerly on the first call for `key`, from a captured
+// CUDA graph afterwards.
+template <typename F>
+int run_graph(nnmg_handle* h, std::tuple<int, int, int> key, cudaStream_t s, F body) {
+  auto it = h->graphs.find(key);
+  if (it != h->graphs.end()) {
+    CK(cudaGraphLaunch(it->second, s));
+    return NNMG_OK;
+  }
+  int& runs = h->runs[key];
+  if (runs == 0) {
+    runs = 1;
+    CK(body(s));
+    return NNMG_OK;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t eb = body(h->cap);
+  cudaError_t ee = cudaStreamEndCapture(h->cap, &g);
+  if (eb != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    set_error(std::string("graph capture failed: ") +
+              cudaGetErrorString(eb != cudaSuccess ? eb : ee));
+    return NNMG_CUDA_ERROR;
+  }
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    set_error(std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    return NNMG_CUDA_ERROR;
+  }
+  h->graphs[key] = ex;
+  CK(cudaGraphLaunch(ex, s));
+  return NNMG_OK;
+}
+
+// ------------------------------------------------------------------ setup
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int n = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {  // Sturm count of eigenvalues < x
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < n; ++i) {
+      d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 300; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (count_below(mid) == n)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+double sum_partial_host(const std::vector<double>& p) {
+  double s = 0.0;
+  for (int b = 0; b < kDotBlocks; ++b) s += p[(size_t)b * kMaxRhs];
+  return s;
+}
+
+int lanczos(nnmg_handle* h, DevLevel& L, cudaStream_t s) {
+  const int64_t n = L.rows;
+  if (L.n_free_nodes == 0) {
+    L.lam_max = 1.0;
+    return NNMG_OK;
+  }
+  std::vector<double> v0((size_t)n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    if (!L.num.constrained[i / L.ncomp]) v0[i] = 1.0 + 0.01 * (double)((i % 17) - 8);
+  double *v, *vp, *w, *u, *part;
+  CK(cudaMalloc(&v, n * sizeof(double)));
+  CK(cudaMalloc(&vp, n * sizeof(double)));
+  CK(cudaMalloc(&w, n * sizeof(double)));
+  CK(cudaMalloc(&u, n * sizeof(double)));
+  CK(cudaMalloc(&part, (size_t)kDotBlocks * kMaxRhs * sizeof(double)));
+  std::vector<double> hp((size_t)kDotBlocks * kMaxRhs);
+  auto dotD = [&](const double* a, const double* b, double* out) -> int {
+    CK(launch_dot_weighted(a, b, L.diag64, part, n, s));
+    CK(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = sum_partial_host(hp);
+    return NNMG_OK;
+  };
+  int rc = NNMG_OK;
+  std::vector<double> al, be;
+  do {
+    CK(cudaMemcpyAsync(v, v0.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(vp, 0, n * sizeof(double), s));
+    CK(cudaMemsetAsync(w, 0, n * sizeof(double), s));
+    double nn;
+    if ((rc = dotD(v, v, &nn)) != NNMG_OK) break;
+    CK(launch_axpy(0.0, v, v, 1.0 / std::sqrt(nn), n, s));
+    double beta = 0.0;
+    for (int j = 0; j < h->opt.lanczos_steps; ++j) {
+      CK(cudaMemsetAsync(u, 0, n * sizeof(double), s));
+      CK(launch_operator<double>(L, v, u, 1, h->opt.lambda, h->opt.mu, s));
+      CK(launch_axpby_dinv(u, L.dinv64, vp, beta, w, n, s));
+      double alpha;
+      if ((rc = dotD(w, v, &alpha)) != NNMG_OK) break;
+      CK(launch_axpy(-alpha, v, w, 1.0, n, s));
+      double ww;
+      if ((rc = dotD(w, w, &ww)) != NNMG_OK) break;
+      beta = std::sqrt(std::max(ww, 0.0));
+      al.push_back(alpha);
+      be.push_back(beta);
+      if (beta == 0.0) break;
+      std::swap(vp, v);                                 // vp <- v
+      CK(launch_axpy(1.0 / beta, w, v, 0.0, n, s));     // v <- w / beta
+    }
+  } while (false);
+  cudaFree(v);
+  cudaFree(vp);
+  cudaFree(w);
+  cudaFree(u);
+  cudaFree(part);
+  if (rc != NNMG_OK) return rc;
+  L.lam_max = tridiag_max_eig(al, be);
+  return NNMG_OK;
+}
+
+int setup_coarse(nnmg_handle* h, DevLevel& L, cudaStream_t s) {
+  std::vector<int32_t> rows;
+  for (int64_t r = 0; r < L.rows; ++r)
+    if (!L.num.constrained[r / L.ncomp]) rows.push_back((int32_t)r);
+  const int n = (int)rows.size();
+  L.n_free_rows = n;
+  CK(dalloc(h, &L.free_rows, std::max(n, 1)));
+  if (n == 0) return NNMG_OK;
+  CK(cudaMemcpy(L.free_rows, rows.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  std::vector<double> A((size_t)n * n, 0.0);
+  const int nb = kMaxRhs;
+  double *X, *Y;
+  CK(cudaMalloc(&X, (size_t)L.rows * nb * sizeof(double)));
+  CK(cudaMalloc(&Y, (size_t)L.rows * nb * sizeof(double)));
+  std::vector<double> hx((size_t)L.rows * nb), hy((size_t)L.rows * nb);
+  int rc = NNMG_OK;
+  for (int j0 = 0; j0 < n && rc == NNMG_OK; j0 += nb) {
+    const int m = std::min(nb, n - j0);
+    std::fill(hx.begin(), hx.end(), 0.0);
+    for (int c = 0; c < m; ++c) hx[(size_t)rows[j0 + c] * m + c] = 1.0;
+    cudaError_t e = cudaMemcpyAsync(X, hx.data(), (size_t)L.rows * m * sizeof(double),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Y, 0, (size_t)L.rows * m * sizeof(double), s);
+    if (e == cudaSuccess) e = launch_operator<double>(L, X, Y, m, h->opt.lambda, h->opt.mu, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hy.data(), Y, (size_t)L.rows * m * sizeof(double),
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error(std::string("coarse assembly: ") + cudaGetErrorString(e));
+      rc = NNMG_CUDA_ERROR;
+      break;
+    }
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < m; ++c) A[(size_t)i * n + j0 + c] = hy[(size_t)rows[i] * m + c];
+  }
+  cudaFree(X);
+  cudaFree(Y);
+  if (rc != NNMG_OK) return rc;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double v = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = v;
+      A[(size_t)j * n + i] = v;
+    }
+  std::vector<double> inv;
+  if (!dense_spd_inverse(A, n, &inv)) {
+    set_error("coarsest operator is not positive definite");
+    return NNMG_CHOLESKY_FAIL;
+  }
+  CK(dalloc(h, &L.coarse_inv, (size_t)n * n));
+  CK(cudaMemcpy(L.coarse_inv, inv.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice));
+  return NNMG_OK;
+}
+
+int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStream_t s) {
+  const nnmg_options& o = h->opt;
+  L.dim = d.dim;
+  L.k = o.degree;
+  L.n1 = o.degree + 1;
+  L.nloc = d.dim == 2 ? L.n1 * L.n1 : L.n1 * L.n1 * L.n1;
+  L.ncomp = o.n_components;
+  L.nmetric = o.n_components == 1 ? d.dim * (d.dim + 1) / 2 : d.dim * d.dim;
+  L.n_vertices = d.n_vertices;
+  L.n_cells = d.n_cells;
+  const int nc4 = 1 << d.dim;
+  for (int64_t i = 0; i < d.n_cells * nc4; ++i) {
+    if (d.cells[i] < 0 || d.cells[i] >= d.n_vertices) {
+      set_error("cell vertex index out of range");
+      return NNMG_INVALID_ARG;
+    }
+  }
+  int rc = number_nodes(d.cells, d.n_cells, d.n_vertices, d.dim, o.degree, d.dirichlet_vertex, &L.num);
+  if (rc != NNMG_OK) return rc;
+  L.n_nodes = L.num.n_nodes;
+  L.rows = L.n_nodes * L.ncomp;
+  L.n_free_nodes = 0;
+  for (auto c : L.num.constrained) L.n_free_nodes += c ? 0 : 1;
+  L.h_vertices.assign(d.vertices, d.vertices + d.n_vertices * d.dim);
+  L.h_cells.assign(d.cells, d.cells + d.n_cells * nc4);
+  CK(dalloc(h, &L.vertices, (size_t)d.n_vertices * d.dim));
+  CK(dalloc(h, &L.cells, (size_t)d.n_cells * nc4));
+  CK(cudaMemcpy(L.vertices, d.vertices, (size_t)d.n_vertices * d.dim * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.cells, d.cells, (size_t)d.n_cells * nc4 * sizeof(int32_t), cudaMemcpyHostToDevice));
+  std::vector<int32_t> masked(L.num.cell_nodes);
+  for (auto& v : masked)
+    if (L.num.constrained[v]) v = -1;
+  CK(dalloc(h, &L.cell_nodes, masked.size()));
+  CK(cudaMemcpy(L.cell_nodes, masked.data(), masked.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(dalloc(h, &L.owner_cell, (size_t)L.n_nodes));
+  CK(dalloc(h, &L.owner_local, (size_t)L.n_nodes));
+  CK(cudaMemcpy(L.owner_cell, L.num.owner_cell.data(), L.n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.owner_local, L.num.owner_local.data(), L.n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
+  std::vector<uint8_t> rf((size_t)L.rows);
+  for (int64_t r = 0; r < L.rows; ++r) rf[r] = L.num.constrained[r / L.ncomp] ? 0 : 1;
+  CK(dalloc(h, &L.row_free, (size_t)L.rows));
+  CK(cudaMemcpy(L.row_free, rf.data(), L.rows, cudaMemcpyHostToDevice));
+  // geometry
+  const size_t nm = (size_t)L.n_cells * L.nmetric * L.nloc;
+  CK(dalloc(h, &L.metric64, nm));
+  CK(dalloc(h, &L.metric32, nm));
+  int* derr;
+  CK(cudaMalloc(&derr, sizeof(int)));
+  CK(cudaMemsetAsync(derr, 0, sizeof(int), s));
+  CK(launch_metric(L, derr, s));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFree(derr);
+  if (herr) {
+    set_error("non-positive Jacobian determinant at a quadrature point");
+    return NNMG_BAD_MESH;
+  }
+  CK(dalloc(h, &L.points, (size_t)L.n_nodes * d.dim));
+  CK(launch_support_points(L, s));
+  CK(dalloc(h, &L.diag64, (size_t)L.rows));
+  CK(dalloc(h, &L.dinv64, (size_t)L.rows));
+  CK(dalloc(h, &L.dinv32, (size_t)L.rows));
+  CK(cudaMemsetAsync(L.diag64, 0, L.rows * sizeof(double), s));
+  CK(launch_diag(L, o.lambda, o.mu, s));
+  CK(launch_finalize_diag(L.diag64, L.row_free, L.dinv64, L.dinv32, L.rows, s));
+  CK(cudaStreamSynchronize(s));
+  return NNMG_OK;
+}
+
+// Locate the free fine nodes of level `fi` in level fi-1 and build the sorted
+// point lists (fine side) and the restriction gather lists (coarse side).
+int setup_transfer(nnmg_handle* h, int fi, cudaStream_t s) {
+  DevLevel& F = h->lv[fi];
+  DevLevel& C = h->lv[fi - 1];
+  const int dim = F.dim;
+  std::vector<int32_t> pts;
+  for (int64_t i = 0; i < F.n_nodes; ++i)
+    if (!F.num.constrained[i]) pts.push_back((int32_t)i);
+  const int64_t np = (int64_t)pts.size();
+  F.n_pts = np;
+  BucketGrid g;
+  std::vector<double> aabb;
+  build_buckets(C.h_vertices.data(), C.h_cells.data(), C.n_cells, dim, &g, &aabb);
+  int32_t *dstart, *dcells, *dpts, *dcell;
+  double *daabb, *dxi;
+  CK(cudaMalloc(&dstart, g.start.size() * sizeof(int32_t)));
+  CK(cudaMalloc(&dcells, std::max<size_t>(g.cells.size(), 1) * sizeof(int32_t)));
+  CK(cudaMalloc(&daabb, aabb.size() * sizeof(double)));
+  CK(cudaMalloc(&dpts, std::max<int64_t>(np, 1) * sizeof(int32_t)));
+  CK(cudaMalloc(&dcell, std::max<int64_t>(np, 1) * sizeof(int32_t)));
+  CK(cudaMalloc(&dxi, std::max<int64_t>(np, 1) * dim * sizeof(double)));
+  CK(cudaMemcpy(dstart, g.start.data(), g.start.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (!g.cells.empty())
+    CK(cudaMemcpy(dcells, g.cells.data(), g.cells.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(daabb, aabb.data(), aabb.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (np) CK(cudaMemcpy(dpts, pts.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(launch_locate(C, F.points, dpts, np, dstart, dcells, daabb, g.geo, dcell, dxi, s));
+  F.h_loc_cell.assign((size_t)np, -1);
+  F.h_loc_xi.assign((size_t)np * dim, 0.0);
+  if (np) {
+    CK(cudaMemcpyAsync(F.h_loc_cell.data(), dcell, np * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(F.h_loc_xi.data(), dxi, np * dim * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dstart);
+  cudaFree(dcells);
+  cudaFree(daabb);
+  cudaFree(dpts);
+  cudaFree(dcell);
+  cudaFree(dxi);
+  for (int64_t p = 0; p < np; ++p) {
+    if (F.h_loc_cell[p] < 0) {
+      set_error("fine support point not located in the coarser mesh");
+      return NNMG_POINT_NOT_FOUND;
+    }
+  }
+  // counting sort by coarse cell (stable: ascending fine node within a cell)
+  std::vector<int32_t> start((size_t)C.n_cells + 1, 0);
+  for (int64_t p = 0; p < np; ++p) start[F.h_loc_cell[p] + 1]++;
+  for (int64_t c = 0; c < C.n_cells; ++c) start[c + 1] += start[c];
+  std::vector<int32_t> fill(start.begin(), start.end() - 1);
+  std::vector<int32_t> snode((size_t)np);
+  std::vector<double> sxi((size_t)np * dim);
+  std::vector<float> sxi32((size_t)np * dim);
+  for (int64_t p = 0; p < np; ++p) {
+    const int32_t q = fill[F.h_loc_cell[p]]++;
+    snode[q] = pts[p];
+    for (int d = 0; d < dim; ++d) {
+      sxi[(size_t)q * dim + d] = F.h_loc_xi[(size_t)p * dim + d];
+      sxi32[(size_t)q * dim + d] = (float)F.h_loc_xi[(size_t)p * dim + d];
+    }
+  }
+  CK(dalloc(h, &F.pt_node, (size_t)np));
+  CK(dalloc(h, &F.pt_xi64, (size_t)np * dim));
+  CK(dalloc(h, &F.pt_xi32, (size_t)np * dim));
+  CK(dalloc(h, &F.cell_pt_start, start.size()));
+  if (np) {
+    CK(cudaMemcpy(F.pt_node, snode.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.pt_xi64, sxi.data(), np * dim * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.pt_xi32, sxi32.data(), np * dim * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(F.cell_pt_start, start.data(), start.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return NNMG_OK;
+}
+
+int setup_gather(nnmg_handle* h, DevLevel& C) {
+  std::vector<int32_t> start((size_t)C.n_nodes + 1, 0);
+  const auto& cn = C.num.cell_nodes;
+  for (size_t i = 0; i < cn.size(); ++i)
+    if (!C.num.constrained[cn[i]]) start[cn[i] + 1]++;
+  for (int64_t n = 0; n < C.n_nodes; ++n) start[n + 1] += start[n];
+  std::vector<int32_t> fill(start.begin(), start.end() - 1), pos((size_t)start.back());
+  for (size_t i = 0; i < cn.size(); ++i)
+    if (!C.num.constrained[cn[i]]) pos[fill[cn[i]]++] = (int32_t)i;
+  CK(dalloc(h, &C.gather_start, start.size()));
+  CK(dalloc(h, &C.gather_pos, std::max<size_t>(pos.size(), 1)));
+  CK(cudaMemcpy(C.gather_start, start.data(), start.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (!pos.empty())
+    CK(cudaMemcpy(C.gather_pos, pos.data(), pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return NNMG_OK;
+}
+
+int check_vec_args(nnmg_handle* h, int level, int precision, int nrhs) {
+  if (!h) {
+    set_error("null handle");
+    return NNMG_INVALID_ARG;
+  }
+  if (level < 0 || level >= (int)h->lv.size()) {
+    set_error("level out of range");
+    return NNMG_INVALID_ARG;
+  }
+  if (precision != NNMG_F32 && precision != NNMG_F64) {
+    set_error("precision must be NNMG_F32 or NNMG_F64");
+    return NNMG_INVALID_ARG;
+  }
+  if (nrhs < 1 || nrhs > h->opt.max_nrhs) {
+    set_error("nrhs must be in 1..max_nrhs");
+    return NNMG_INVALID_ARG;
+  }
+  return NNMG_OK;
+}
+
+void destroy_impl(nnmg_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_sc) cudaFreeHost(h->h_sc);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void nnmg_default_options(nnmg_options* o) {
+  if (!o) return;
+  o->degree = 1;
+  o->n_components = 1;
+  o->lambda = 1.0;
+  o->mu = 1.0;
+  o->cheb_degree = 3;
+  o->smoothing_range = 20.0;
+  o->lanczos_steps = 12;
+  o->eig_safety = 1.2;
+  o->max_nrhs = 16;
+}
+
+const char* nnmg_last_error(void) { return get_error(); }
+
+int nnmg_setup_hierarchy(const nnmg_level_desc* levels, int n_levels, const nnmg_options* opt,
+                         void* stream, nnmg_handle** out) {
+  set_error("");
+  if (!out || !levels || !opt || n_levels < 1) {
+    set_error("null argument or n_levels < 1");
+    return NNMG_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (opt->degree < 1 || opt->degree > kMaxDegree || (opt->n_components != 1 && opt->n_components != 3) ||
+      opt->cheb_degree < 1 || opt->lanczos_steps < 1 || opt->max_nrhs < 1 || opt->max_nrhs > kMaxRhs ||
+      !(opt->smoothing_range > 1.0) || !(opt->eig_safety > 0.0)) {
+    set_error("invalid options");
+    return NNMG_INVALID_ARG;
+  }
+  for (int l = 0; l < n_levels; ++l) {
+    const nnmg_level_desc& d = levels[l];
+    if ((d.dim != 2 && d.dim != 3) || d.dim != levels[0].dim || d.n_cells < 1 || d.n_vertices < 1 ||
+        !d.vertices || !d.cells || (opt->n_components == 3 && d.dim != 3)) {
+      set_error("invalid level description");
+      return NNMG_INVALID_ARG;
+    }
+  }
+  nnmg_handle* h = nullptr;
+  try {
+    h = new nnmg_handle();
+    h->opt = *opt;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("cannot create capture stream");
+      destroy_impl(h);
+      return NNMG_CUDA_ERROR;
+    }
+    h->lv.resize(n_levels);
+    int rc = NNMG_OK;
+    for (int l = 0; l < n_levels && rc == NNMG_OK; ++l) rc = setup_level(h, levels[l], h->lv[l], s);
+    for (int l = 1; l < n_levels && rc == NNMG_OK; ++l) rc = setup_transfer(h, l, s);
+    for (int l = 0; l + 1 < n_levels && rc == NNMG_OK; ++l) rc = setup_gather(h, h->lv[l]);
+    for (int l = 1; l < n_levels && rc == NNMG_OK; ++l) {
+      rc = lanczos(h, h->lv[l], s);
+      DevLevel& L = h->lv[l];
+      L.cheb_b = h->opt.eig_safety * L.lam_max;
+      L.cheb_a = L.cheb_b / h->opt.smoothing_range;
+    }
+    if (rc == NNMG_OK) rc = setup_coarse(h, h->lv[0], s);
+    if (rc == NNMG_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("setup: stream synchronize failed");
+      rc = NNMG_CUDA_ERROR;
+    }
+    if (rc != NNMG_OK) {
+      std::string msg = get_error();
+      destroy_impl(h);
+      set_error(msg);
+      return rc;
+    }
+    *out = h;
+    return NNMG_OK;
+  } catch (const std::bad_alloc&) {
+    if (h) destroy_impl(h);
+    set_error("host allocation failed");
+    return NNMG_OUT_OF_MEMORY;
+  }
+}
+
+int nnmg_destroy(nnmg_handle* h) {
+  if (h) destroy_impl(h);
+  return NNMG_OK;
+}
+
+int nnmg_n_levels(const nnmg_handle* h) { return h ? (int)h->lv.size() : 0; }
+
+int nnmg_level_info(const nnmg_handle* h, int level, int64_t* n_nodes, int64_t* n_free,
+                    int64_t* n_cells) {
+  if (!h || level < 0 || level >= (int)h->lv.size()) {
+    set_error("bad handle or level");
+    return NNMG_INVALID_ARG;
+  }
+  const DevLevel& L = h->lv[level];
+  if (n_nodes) *n_nodes = L.n_nodes;
+  if (n_free) *n_free = L.n_free_nodes;
+  if (n_cells) *n_cells = L.n_cells;
+  return NNMG_OK;
+}
+
+size_t nnmg_hierarchy_bytes(const nnmg_handle* h) { return h ? h->bytes : 0; }
+
+size_t nnmg_solve_bytes(const nnmg_handle* h, int nrhs) {
+  if (!h) return 0;
+  size_t b = 0;
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    const DevLevel& L = h->lv[l];
+    size_t per = (size_t)L.rows * nrhs * (l ? 4 : 2);
+    if (l) per += (size_t)h->lv[l - 1].n_cells * h->lv[l - 1].nloc * L.ncomp * nrhs;
+    b += per * (sizeof(float) + sizeof(double));
+  }
+  b += (size_t)h->lv.back().rows * nrhs * 5 * sizeof(double);
+  return b;
+}
+
+int nnmg_support_points(const nnmg_handle* h, int level, double* pts) {
+  if (!h || !pts || level < 0 || level >= (int)h->lv.size()) {
+    set_error("bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  const DevLevel& L = h->lv[level];
+  NNMG_CUDA(cudaMemcpy(pts, L.points, (size_t)L.n_nodes * L.dim * sizeof(double), cudaMemcpyDeviceToHost));
+  return NNMG_OK;
+}
+
+int nnmg_constrained_nodes(const nnmg_handle* h, int level, uint8_t* flags) {
+  if (!h || !flags || level < 0 || level >= (int)h->lv.size()) {
+    set_error("bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  const DevLevel& L = h->lv[level];
+  std::memcpy(flags, L.num.constrained.data(), (size_t)L.n_nodes);
+  return NNMG_OK;
+}
+
+int nnmg_cell_nodes(const nnmg_handle* h, int level, int32_t* cn) {
+  if (!h || !cn || level < 0 || level >= (int)h->lv.size()) {
+    set_error("bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  const DevLevel& L = h->lv[level];
+  std::memcpy(cn, L.num.cell_nodes.data(), L.num.cell_nodes.size() * sizeof(int32_t));
+  return NNMG_OK;
+}
+
+int nnmg_quadrature_points(const nnmg_handle* h, int level, double* xq) {
+  if (!h || !xq || level < 0 || level >= (int)h->lv.size()) {
+    set_error("bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  const DevLevel& L = h->lv[level];
+  const size_t n = (size_t)L.n_cells * L.nloc * L.dim;
+  double* d;
+  NNMG_CUDA(cudaMalloc(&d, n * sizeof(double)));
+  cudaError_t e = launch_quad_points(L, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(xq, d, n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  NNMG_CUDA(e);
+  return NNMG_OK;
+}
+
+int nnmg_transfer_points(const nnmg_handle* h, int fine_level, int32_t* cell, double* xi) {
+  if (!h || fine_level < 1 || fine_level >= (int)h->lv.size()) {
+    set_error("bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  const DevLevel& F = h->lv[fine_level];
+  if (cell) std::memcpy(cell, F.h_loc_cell.data(), F.h_loc_cell.size() * sizeof(int32_t));
+  if (xi) std::memcpy(xi, F.h_loc_xi.data(), F.h_loc_xi.size() * sizeof(double));
+  return NNMG_OK;
+}
+
+int nnmg_eigen_estimates(const nnmg_handle* h, double* lam) {
+  if (!h || !lam) {
+    set_error("bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  for (size_t l = 0; l < h->lv.size(); ++l) lam[l] = l ? h->lv[l].lam_max : 0.0;
+  return NNMG_OK;
+}
+
+int nnmg_load_vector(nnmg_handle* h, int level, const double* f, int f_per_qp, double* b,
+                     int nrhs, int col, void* stream) {
+  int rc = check_vec_args(h, level, NNMG_F64, nrhs);
+  if (rc) return rc;
+  if (!f || !b || col < 0 || col >= nrhs) {
+    set_error("bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevLevel& L = h->lv[level];
+  const size_t nf = f_per_qp ? (size_t)L.n_cells * L.nloc * L.ncomp : (size_t)L.ncomp;
+  double* df;
+  NNMG_CUDA(cudaMalloc(&df, nf * sizeof(double)));
+  cudaError_t e = cudaMemcpyAsync(df, f, nf * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemset2DAsync(b + col, (size_t)nrhs * sizeof(double), 0, sizeof(double), (size_t)L.rows, s);
+  if (e == cudaSuccess) e = launch_load_vector(L, df, f_per_qp, b, nrhs, col, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(df);
+  NNMG_CUDA(e);
+  return NNMG_OK;
+}
+
+int nnmg_apply_operator(nnmg_handle* h, int level, int precision, const void* x, void* y,
+                        int nrhs, void* stream) {
+  int rc = check_vec_args(h, level, precision, nrhs);
+  if (rc) return rc;
+  if (!x || !y || x == y) {
+    set_error("x and y must be distinct device vectors");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevLevel& L = h->lv[level];
+  const size_t ts = precision == NNMG_F64 ? sizeof(double) : sizeof(float);
+  NNMG_CUDA(cudaMemsetAsync(y, 0, (size_t)L.rows * nrhs * ts, s));
+  if (precision == NNMG_F64)
+    NNMG_CUDA(launch_operator<double>(L, (const double*)x, (double*)y, nrhs, h->opt.lambda, h->opt.mu, s));
+  else
+    NNMG_CUDA(launch_operator<float>(L, (const float*)x, (float*)y, nrhs, h->opt.lambda, h->opt.mu, s));
+  return NNMG_OK;
+}
+
+int nnmg_prolongate(nnmg_handle* h, int fine_level, int precision, const void* coarse, void* fine,
+                    int nrhs, void* stream) {
+  int rc = check_vec_args(h, fine_level, precision, nrhs);
+  if (rc) return rc;
+  if (fine_level < 1 || !coarse || !fine) {
+    set_error("fine_level must be >= 1 and vectors non-null");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevLevel& F = h->lv[fine_level];
+  const DevLevel& C = h->lv[fine_level - 1];
+  const size_t ts = precision == NNMG_F64 ? sizeof(double) : sizeof(float);
+  NNMG_CUDA(cudaMemsetAsync(fine, 0, (size_t)F.rows * nrhs * ts, s));
+  if (precision == NNMG_F64)
+    NNMG_CUDA(launch_prolongate_add<double>(F, C, (const double*)coarse, (double*)fine, nrhs, s));
+  else
+    NNMG_CUDA(launch_prolongate_add<float>(F, C, (const float*)coarse, (float*)fine, nrhs, s));
+  return NNMG_OK;
+}
+
+int nnmg_restrict(nnmg_handle* h, int fine_level, int precision, const void* fine, void* coarse,
+                  int nrhs, void* stream) {
+  int rc = check_vec_args(h, fine_level, precision, nrhs);
+  if (rc) return rc;
+  if (fine_level < 1 || !coarse || !fine) {
+    set_error("fine_level must be >= 1 and vectors non-null");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevLevel& F = h->lv[fine_level];
+  const DevLevel& C = h->lv[fine_level - 1];
+  if (precision == NNMG_F64) {
+    if ((rc = ensure_work<double>(h))) return rc;
+    NNMG_CUDA(launch_restrict<double>(F, C, (const double*)fine, (double*)coarse,
+                                      h->w64.scratch[fine_level], nrhs, s));
+  } else {
+    if ((rc = ensure_work<float>(h))) return rc;
+    NNMG_CUDA(launch_restrict<float>(F, C, (const float*)fine, (float*)coarse,
+                                     h->w32.scratch[fine_level], nrhs, s));
+  }
+  return NNMG_OK;
+}
+
+int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs, void* stream) {
+  int rc = check_vec_args(h, 0, precision, nrhs);
+  if (rc) return rc;
+  if (!r || !z) {
+    set_error("null vector");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int top = (int)h->lv.size() - 1;
+  const size_t n = (size_t)h->lv[top].rows * nrhs;
+  if (precision == NNMG_F64) {
+    if ((rc = ensure_work<double>(h))) return rc;
+    NNMG_CUDA(cudaMemcpyAsync(h->w64.f[top], r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (top == 0) NNMG_CUDA(cudaMemsetAsync(h->w64.x[0], 0, n * sizeof(double), s));
+    rc = run_graph(h, {0, NNMG_F64, nrhs}, s, [&](cudaStream_t st) {
+      return enqueue_vcycle<double>(h, h->w64.f[top], nrhs, st);
+    });
+    if (rc) return rc;
+    NNMG_CUDA(cudaMemcpyAsync(z, h->w64.x[top], n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    if ((rc = ensure_work<float>(h))) return rc;
+    NNMG_CUDA(cudaMemcpyAsync(h->w32.f[top], r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (top == 0) NNMG_CUDA(cudaMemsetAsync(h->w32.x[0], 0, n * sizeof(float), s));
+    rc = run_graph(h, {0, NNMG_F32, nrhs}, s, [&](cudaStream_t st) {
+      return enqueue_vcycle<float>(h, h->w32.f[top], nrhs, st);
+    });
+    if (rc) return rc;
+    NNMG_CUDA(cudaMemcpyAsync(z, h->w32.x[top], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  return NNMG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// PCG from x0 = 0 on device right-hand sides b; the solution stays in h->px.
+int pcg_run(nnmg_handle* h, int mode, const double* b, int nrhs, double rtol, int maxit,
+            int* iters_out, double* relres_out, cudaStream_t s) {
+  int rc;
+  if ((rc = ensure_pcg(h))) return rc;
+  if ((rc = (mode == NNMG_FP32_MG_FP64_CG ? ensure_work<float>(h) : ensure_work<double>(h)))) return rc;
+  const DevLevel& L = h->lv.back();
+  NNMG_CUDA(launch_pcg_init(b, L.row_free, h->pr, h->px, h->pp, h->partial, L.rows, nrhs, s));
+  NNMG_CUDA(launch_pcg_start(h->sc, h->partial, nrhs, rtol, s));
+  NNMG_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+  NNMG_CUDA(cudaStreamSynchronize(s));
+  bool active = h->h_sc->any_active != 0;
+  for (int it = 0; it < maxit && active; ++it) {
+    rc = run_graph(h, {1, mode, nrhs}, s, [&](cudaStream_t st) {
+      return enqueue_pcg_iter(h, mode, nrhs, st);
+    });
+    if (rc) return rc;
+    NNMG_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    NNMG_CUDA(cudaStreamSynchronize(s));
+    active = h->h_sc->any_active != 0;
+  }
+  const PcgScalars& sc = *h->h_sc;
+  bool conv = true;
+  for (int q = 0; q < nrhs; ++q) {
+    if (iters_out) iters_out[q] = sc.iters[q];
+    const double rel = sc.bnorm[q] > 0 ? sc.rnorm[q] / sc.bnorm[q] : 0.0;
+    if (relres_out) relres_out[q] = rel;
+    conv = conv && (rel <= rtol);
+  }
+  if (sc.breakdown) {
+    set_error("PCG breakdown (p.Ap <= 0 or non-finite scalar)");
+    return NNMG_BREAKDOWN;
+  }
+  if (!conv) {
+    set_error("PCG did not reach rtol within maxit");
+    return NNMG_NOT_CONVERGED;
+  }
+  return NNMG_OK;
+}
+
+int pcg_args(nnmg_handle* h, int mode, int nrhs, double rtol, int maxit) {
+  int rc = check_vec_args(h, 0, NNMG_F64, nrhs);
+  if (rc) return rc;
+  if ((mode != NNMG_FP64_MG && mode != NNMG_FP32_MG_FP64_CG) || !(rtol > 0.0) || maxit < 1) {
+    set_error("bad mode, rtol or maxit");
+    return NNMG_INVALID_ARG;
+  }
+  return NNMG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int nnmg_pcg_solve(nnmg_handle* h, int mode, const double* b, double* x, int nrhs, double rtol,
+                   int maxit, int* iters_out, double* relres_out, void* stream) {
+  int rc = pcg_args(h, mode, nrhs, rtol, maxit);
+  if (rc) return rc;
+  if (!b || !x) {
+    set_error("null vector");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = pcg_run(h, mode, b, nrhs, rtol, maxit, iters_out, relres_out, s);
+  if (rc != NNMG_OK && rc != NNMG_NOT_CONVERGED && rc != NNMG_BREAKDOWN) return rc;
+  const size_t n = (size_t)h->lv.back().rows * nrhs * sizeof(double);
+  NNMG_CUDA(cudaMemcpyAsync(x, h->px, n, cudaMemcpyDeviceToDevice, s));
+  return rc;
+}
+
+int nnmg_pcg_solve_host(nnmg_handle* h, int mode, const double* b_host, double* x_host, int nrhs,
+                        double rtol, int maxit, int* iters_out, double* relres_out, void* stream) {
+  int rc = pcg_args(h, mode, nrhs, rtol, maxit);
+  if (rc) return rc;
+  if (!b_host || !x_host) {
+    set_error("null host vector");
+    return NNMG_INVALID_ARG;
+  }
+  if ((rc = ensure_pcg(h))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)h->lv.back().rows * nrhs * sizeof(double);
+  NNMG_CUDA(cudaMemcpyAsync(h->pb, b_host, n, cudaMemcpyHostToDevice, s));
+  rc = pcg_run(h, mode, h->pb, nrhs, rtol, maxit, iters_out, relres_out, s);
+  if (rc != NNMG_OK && rc != NNMG_NOT_CONVERGED && rc != NNMG_BREAKDOWN) return rc;
+  cudaError_t e = cudaMemcpyAsync(x_host, h->px, n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  NNMG_CUDA(e);
+  return rc;
+}
+
+}  // extern "C"

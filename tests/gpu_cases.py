@@ -1,0 +1,39 @@
+"""Shared builders for the GPU parity tests: the same seeded levels go to the
+oracle and to the CUDA library."""
+import functools
+
+import numpy as np
+
+from synthetic import config_levels
+from synthetic.meshes import CONFIGS
+from tests.oracle_meshes import box_level, scramble
+
+# name -> (levels factory, degree, ncomp, lame, cheb, nrhs)
+CASES = {
+    "c1_q1": (lambda: config_levels("c1_2d_q1"), 1, 1, (1.0, 1.0), 3, 1),
+    "c1_q3": (lambda: config_levels("c1_2d_q1", n_levels=2), 3, 1, (1.0, 1.0), 3, 3),
+    "c2_q2_3lev": (lambda: config_levels("c2_3d_q2", n_levels=3), 2, 1, (1.0, 1.0), 3, 8),
+    "c3_q4_2lev": (lambda: config_levels("c3_3d_q4_deformed", n_levels=2), 4, 1, (1.0, 1.0), 5, 4),
+    "c4_elast": (lambda: config_levels("c4_3d_q2_elasticity"), 2, 3, (10.0, 1.0), 4, 1),
+    "scrambled_q3": (lambda: [scramble(box_level((2, 2, 2), alpha=0.1, seed=3), 5),
+                              scramble(box_level((5, 4, 3), alpha=0.2, seed=4), 6)], 3, 1,
+                     (1.0, 1.0), 3, 2),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_case(name):
+    from oracle.hierarchy import OracleHierarchy
+    lv, k, nc, lame, cheb, nrhs = CASES[name]
+    levels = lv()
+    return levels, OracleHierarchy(levels, k, nc, lame, cheb)
+
+
+def gpu_case(name, levels):
+    from paper_2412_10910_gb300 import nnmg
+    _, k, nc, lame, cheb, nrhs = CASES[name]
+    return nnmg.Hierarchy(levels, k, nc, lame, cheb, max_nrhs=16)
+
+
+def rng_vec(rows, nrhs, seed):
+    return np.random.default_rng(seed).standard_normal((rows, nrhs))

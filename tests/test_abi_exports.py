@@ -1,0 +1,45 @@
+"""The C library loads without a GPU and exports every symbol include/nnmg.h declares."""
+import os
+import re
+
+from paper_2412_10910_gb300 import _abi
+
+HEADER = os.path.join(os.path.dirname(__file__), "..", "include", "nnmg.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nnmg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported_and_bound():
+    lib = _abi.load()
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _abi.PROTOTYPES, n
+
+
+def test_default_options_host_only():
+    import ctypes as C
+    lib = _abi.load()
+    o = _abi.Options()
+    lib.nnmg_default_options(C.byref(o))
+    assert (o.degree, o.cheb_degree, o.lanczos_steps, o.max_nrhs) == (1, 3, 12, 16)
+    assert o.smoothing_range == 20.0 and o.eig_safety == 1.2
+
+
+def test_invalid_arguments_rejected_without_gpu_work():
+    import ctypes as C
+    lib = _abi.load()
+    h = C.c_void_p()
+    o = _abi.Options()
+    lib.nnmg_default_options(C.byref(o))
+    assert lib.nnmg_setup_hierarchy(None, 0, C.byref(o), None, C.byref(h)) == _abi.INVALID_ARG
+    assert b"n_levels" in lib.nnmg_last_error()
+    o.degree = 7
+    d = (_abi.LevelDesc * 1)()
+    assert lib.nnmg_setup_hierarchy(d, 1, C.byref(o), None, C.byref(h)) == _abi.INVALID_ARG
+    assert lib.nnmg_n_levels(None) == 0 and lib.nnmg_hierarchy_bytes(None) == 0
