@@ -122,10 +122,11 @@ def kernels_per_solve(n_levels, cheb, iters):
     return 2 + iters * ((n_levels - 1) * per_level + 1 + 9)
 
 
-def cpu_baseline_sample(nrhs_sample=1, quiet=True):
+def cpu_baseline_sample(nrhs_sample=8, steps=1, warmup=0):
     """Time the FP64 oracle (as it stands) on a bounded sample of the workload in
     a single-threaded subprocess: the three coarsest levels of the same family
-    (finest 27^3 Q2 cells), f = 1, FP32 V-cycle inside FP64 CG."""
+    (finest 27^3 Q2 cells), f = 1 in every column, FP32 V-cycle inside FP64 CG.
+    The oracle hierarchy is built once (untimed); each step is one solve."""
     code = r"""
 import json, sys, time, numpy as np
 sys.path.insert(0, %r)
@@ -136,43 +137,42 @@ H = OracleHierarchy(lv, 2, cheb_degree=3)
 top = len(H.levels) - 1
 b = H.load_vector(top, lambda x: np.ones((len(x), 1)))
 B = np.stack([b] * %d, axis=1)
-t = time.perf_counter()
-x, its, rel, tr = H.pcg(B, "fp32", rtol=1e-8)
-dt = time.perf_counter() - t
-print(json.dumps({"seconds": dt, "free": int(H.levels[top].free_dofs.size), "nrhs": %d,
+for _ in range(%d):
+    H.pcg(B, "fp32", rtol=1e-8)
+ts = []
+for _ in range(%d):
+    t = time.perf_counter()
+    x, its, rel, tr = H.pcg(B, "fp32", rtol=1e-8)
+    ts.append(time.perf_counter() - t)
+print(json.dumps({"seconds": ts, "free": int(H.levels[top].free_dofs.size), "nrhs": %d,
                   "iters": [int(i) for i in its]}))
-""" % (ROOT, nrhs_sample, nrhs_sample)
+""" % (ROOT, nrhs_sample, warmup, steps, nrhs_sample)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=900)
+                       timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    v = d["free"] * d["nrhs"] / d["seconds"]
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+    sec = statistics.mean(d["seconds"])
+    v = d["free"] * d["nrhs"] / sec
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds_per_step": sec,
             "sample": (f"FP64 numpy/scipy oracle, single thread, same family with the 3 coarsest "
                        f"levels (finest 27^3 Q2 cells, {d['free']} free DoFs), {d['nrhs']} RHS f=1, "
-                       f"FP32 V-cycle in FP64 PCG to 1e-8, {d['iters']} iterations, "
-                       f"{d['seconds']:.1f} s")}
+                       f"FP32 V-cycle in FP64 PCG to 1e-8, {d['iters'][0]} iterations, "
+                       f"{sec:.1f} s per solve")}
 
 
 def run_reference(args, rank, world):
+    """Reference arm: the oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
         return
-    vals = []
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; warm-up steps are not repeated
-    last = None
-    for _ in range(args.steps):
-        last = cpu_baseline_sample(1)
-        vals.append(last["value"])
-    v = statistics.mean(vals)
-    ms = 1e3 * (last and float(last["sample"].split(", ")[-1].split(" s")[0]))
+    cb = cpu_baseline_sample(8, steps=args.steps, warmup=args.warmup)
+    v = cb["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cb["seconds_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle: bounded sample)"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": v,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": v,
                              "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["solve", "solve64", "vcycle", "op64", "op32"], default=None,
+                    help="run only one timed section (for profiler launch lists)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -230,6 +232,32 @@ def main():
 
     def solve(mode):
         return H.pcg(b, x, mode=mode, rtol=1e-8, maxit=100)
+
+    if args.only:
+        fns = {"solve": lambda: solve(_abi.FP32_MG_FP64_CG), "solve64": lambda: solve(_abi.FP64_MG)}
+        if args.only in ("vcycle",):
+            r32 = torch.randn(rows, nrhs, dtype=torch.float32, device="cuda")
+            z32 = torch.empty_like(r32)
+            fns["vcycle"] = lambda: H.vcycle(r32, z32)
+        if args.only in ("op64", "op32"):
+            dt = torch.float64 if args.only == "op64" else torch.float32
+            xo = torch.randn(rows, nrhs, dtype=dt, device="cuda")
+            yo = torch.empty_like(xo)
+            fns[args.only] = lambda: H.apply(top, xo, yo)
+        fn = fns[args.only]
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        if rank == 0:
+            print(json.dumps({"only": args.only, "ms_per_step": e0.elapsed_time(e1) / args.steps}))
+        H.close()
+        return
 
     def timed(fn, k, w):
         for _ in range(w):
@@ -335,7 +363,7 @@ def main():
         "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_kind": peak_kind,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(1)
+        line["cpu_baseline"] = cpu_baseline_sample(8)
     if rank == 0:
         print(json.dumps(line), flush=True)
     H.close()

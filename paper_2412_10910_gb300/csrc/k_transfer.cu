@@ -139,24 +139,41 @@ __global__ void restrict2_kernel(const T* __restrict__ buf, const int32_t* __res
   rc[e] = s;
 }
 
-// z[free_i] = sum_j Ainv[i][j] r[free_j], one warp per free row, FP64 accumulation.
+// z[free_i] = sum_j Ainv[i][j] r[free_j] in FP64: one warp per free row, 8 rows
+// per block; the gathered right-hand sides pass through shared memory in tiles
+// of kCoarseTile rows, stored column-major so that lanes read distinct banks.
+constexpr int kCoarseRows = 8;
+constexpr int kCoarseTile = 256;
+
 template <typename TI, typename TO>
-__global__ void coarse_solve_kernel(const double* __restrict__ Ainv, const int32_t* __restrict__ rows,
-                                    int n, const TI* __restrict__ r, TO* __restrict__ z, int nrhs) {
-  const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (w >= n) return;
+__global__ void __launch_bounds__(32 * kCoarseRows) coarse_solve_kernel(
+    const double* __restrict__ Ainv, const int32_t* __restrict__ rows, int n,
+    const TI* __restrict__ r, TO* __restrict__ z, int nrhs) {
+  __shared__ double sr[kMaxRhs * kCoarseTile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kCoarseRows + warp;
   double acc[kMaxRhs];
 #pragma unroll
   for (int q = 0; q < kMaxRhs; ++q) acc[q] = 0.0;
-  const double* arow = Ainv + (int64_t)w * n;
-  for (int j = lane; j < n; j += 32) {
-    const double a = arow[j];
-    const int64_t rj = (int64_t)rows[j] * nrhs;
+  for (int j0 = 0; j0 < n; j0 += kCoarseTile) {
+    const int nt = min(kCoarseTile, n - j0);
+    for (int t = threadIdx.x; t < nt * nrhs; t += blockDim.x) {
+      const int jj = t / nrhs, q = t - jj * nrhs;
+      sr[q * kCoarseTile + jj] = (double)r[(int64_t)rows[j0 + jj] * nrhs + q];
+    }
+    __syncthreads();
+    if (i < n) {
+      const double* arow = Ainv + (int64_t)i * n + j0;
+      for (int jj = lane; jj < nt; jj += 32) {
+        const double a = arow[jj];
 #pragma unroll
-    for (int q = 0; q < kMaxRhs; ++q)
-      if (q < nrhs) acc[q] += a * (double)r[rj + q];
+        for (int q = 0; q < kMaxRhs; ++q)
+          if (q < nrhs) acc[q] += a * sr[q * kCoarseTile + jj];
+      }
+    }
+    __syncthreads();
   }
+  if (i >= n) return;
 #pragma unroll
   for (int q = 0; q < kMaxRhs; ++q) {
     if (q < nrhs) {
@@ -167,7 +184,7 @@ __global__ void coarse_solve_kernel(const double* __restrict__ Ainv, const int32
     }
   }
   if (lane == 0) {
-    const int64_t ri = (int64_t)rows[w] * nrhs;
+    const int64_t ri = (int64_t)rows[i] * nrhs;
     for (int q = 0; q < nrhs; ++q) z[ri + q] = (TO)acc[q];
   }
 }
@@ -262,8 +279,8 @@ cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const 
 template <typename TI, typename TO>
 cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs, cudaStream_t s) {
   if (L.n_free_rows == 0) return cudaSuccess;
-  const int64_t threads = (int64_t)L.n_free_rows * 32;
-  coarse_solve_kernel<TI, TO><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+  const unsigned blocks = (unsigned)((L.n_free_rows + kCoarseRows - 1) / kCoarseRows);
+  coarse_solve_kernel<TI, TO><<<blocks, 32 * kCoarseRows, 0, s>>>(
       L.coarse_inv, L.free_rows, L.n_free_rows, r, z, nrhs);
   return cudaGetLastError();
 }

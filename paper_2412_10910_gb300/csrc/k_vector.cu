@@ -18,12 +18,16 @@ inline unsigned vblocks(int64_t n) {
   return (unsigned)b;
 }
 
+// Vectors handled here hold fewer than 2^31 elements (checked by the
+// launchers), so element and row indices use 32-bit unsigned arithmetic; the
+// row of element e is e / nrhs.
+
 template <typename T>
 __global__ void cheb_init_kernel(const T* __restrict__ f, const T* __restrict__ dinv,
                                  T* __restrict__ d, T* __restrict__ x, T c, int64_t n, int nrhs) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const T v = c * dinv[e / nrhs] * f[e];
+  const unsigned un = (unsigned)n, ur = (unsigned)nrhs;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < un; e += gridDim.x * blockDim.x) {
+    const T v = c * dinv[e / ur] * f[e];
     d[e] = v;
     x[e] = v;
   }
@@ -34,11 +38,11 @@ template <typename T>
 __global__ void cheb_step_kernel(const T* __restrict__ f, T* __restrict__ t,
                                  const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x,
                                  T cd, T cr, int64_t n, int nrhs) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  const unsigned un = (unsigned)n, ur = (unsigned)nrhs;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < un; e += gridDim.x * blockDim.x) {
     const T r = f[e] - t[e];
     t[e] = T(0);
-    const T dn = cd * d[e] + cr * dinv[e / nrhs] * r;
+    const T dn = cd * d[e] + cr * dinv[e / ur] * r;
     d[e] = dn;
     x[e] += dn;
   }
@@ -47,8 +51,8 @@ __global__ void cheb_step_kernel(const T* __restrict__ f, T* __restrict__ t,
 template <typename T>
 __global__ void residual_kernel(const T* __restrict__ f, T* __restrict__ t, T* __restrict__ r,
                                 int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n;
+       e += gridDim.x * blockDim.x) {
     r[e] = f[e] - t[e];
     t[e] = T(0);
   }
@@ -56,28 +60,28 @@ __global__ void residual_kernel(const T* __restrict__ f, T* __restrict__ t, T* _
 
 template <typename TI, typename TO>
 __global__ void cast_kernel(const TI* __restrict__ a, TO* __restrict__ b, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n;
+       e += gridDim.x * blockDim.x)
     b[e] = (TO)a[e];
 }
 
-// block reduction of nrhs per-thread values into partial[blockIdx.x][kMaxRhs]
-__device__ __forceinline__ void block_reduce_store(double (&v)[kMaxRhs], int nrhs, double* partial) {
-  __shared__ double sh[kDotThreads / 32][kMaxRhs];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < kMaxRhs; ++q) {
-    if (q < nrhs) {
-      double s = v[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) sh[wid][q] = s;
-    }
-  }
+// Dot-product layout: a block has kDotThreads - (kDotThreads % nrhs) active
+// threads and the grid stride is a multiple of nrhs, so thread t always visits
+// column t % nrhs.  Each block writes one partial sum per column to
+// partial[block][column]; partials are added in block order by
+// sum_partials_warp.  Both steps have a fixed order: results are reproducible.
+__device__ __forceinline__ unsigned dot_threads(int nrhs) {
+  return kDotThreads - (kDotThreads % (unsigned)nrhs);
+}
+
+__device__ __forceinline__ void block_store_partials(double v, int nrhs, double* partial) {
+  __shared__ double sh[kDotThreads];
+  const unsigned active = dot_threads(nrhs);
+  sh[threadIdx.x] = threadIdx.x < active ? v : 0.0;
   __syncthreads();
-  if (threadIdx.x < nrhs) {
+  if (threadIdx.x < (unsigned)nrhs) {
     double s = 0.0;
-    for (int w = 0; w < kDotThreads / 32; ++w) s += sh[w][threadIdx.x];
+    for (unsigned t = threadIdx.x; t < active; t += nrhs) s += sh[t];
     partial[blockIdx.x * kMaxRhs + threadIdx.x] = s;
   }
 }
@@ -87,102 +91,114 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const double* __restri
                                                           const TB* __restrict__ b,
                                                           double* __restrict__ partial,
                                                           int64_t rows, int nrhs) {
-  double v[kMaxRhs];
-#pragma unroll
-  for (int q = 0; q < kMaxRhs; ++q) v[q] = 0.0;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
-       r += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < kMaxRhs; ++q)
-      if (q < nrhs) v[q] += a[r * nrhs + q] * (double)b[r * nrhs + q];
-  }
-  block_reduce_store(v, nrhs, partial);
+  const unsigned act = dot_threads(nrhs);
+  const unsigned n = (unsigned)(rows * nrhs);
+  double v = 0.0;
+  if (threadIdx.x < act)
+    for (unsigned e = blockIdx.x * act + threadIdx.x; e < n; e += gridDim.x * act)
+      v += a[e] * (double)b[e];
+  block_store_partials(v, nrhs, partial);
 }
 
 __global__ void __launch_bounds__(kDotThreads) pcg_init_kernel(
     const double* __restrict__ b, const uint8_t* __restrict__ row_free, double* __restrict__ r,
     double* __restrict__ x, double* __restrict__ p, double* __restrict__ partial, int64_t rows,
     int nrhs) {
-  double v[kMaxRhs];
-#pragma unroll
-  for (int q = 0; q < kMaxRhs; ++q) v[q] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const bool fr = row_free[i] != 0;
-#pragma unroll
-    for (int q = 0; q < kMaxRhs; ++q) {
-      if (q < nrhs) {
-        const double bv = fr ? b[i * nrhs + q] : 0.0;
-        r[i * nrhs + q] = bv;
-        x[i * nrhs + q] = 0.0;
-        p[i * nrhs + q] = 0.0;
-        v[q] += bv * bv;
-      }
+  const unsigned act = dot_threads(nrhs);
+  const unsigned n = (unsigned)(rows * nrhs);
+  double v = 0.0;
+  if (threadIdx.x < act)
+    for (unsigned e = blockIdx.x * act + threadIdx.x; e < n; e += gridDim.x * act) {
+      const double bv = row_free[e / (unsigned)nrhs] ? b[e] : 0.0;
+      r[e] = bv;
+      x[e] = 0.0;
+      p[e] = 0.0;
+      v += bv * bv;
     }
-  }
-  block_reduce_store(v, nrhs, partial);
+  block_store_partials(v, nrhs, partial);
 }
 
-__device__ __forceinline__ double sum_partials(const double* partial, int q) {
+// Sum of the kDotBlocks partials of column q, by one warp (lanes take blocks
+// lane, lane+32, ...; then a fixed butterfly).  Every lane returns the total.
+__device__ __forceinline__ double sum_partials_warp(const double* partial, int q) {
+  const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int bk = 0; bk < kDotBlocks; ++bk) s += partial[bk * kMaxRhs + q];
+  for (int bk = lane; bk < kDotBlocks; bk += 32) s += partial[bk * kMaxRhs + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
+// Scalar kernels run one warp per column (blockDim = 32 * kMaxRhs).
 __global__ void pcg_start_kernel(PcgScalars* sc, const double* partial, int nrhs, double rtol) {
-  if (threadIdx.x != 0) return;
-  int any = 0;
-  for (int q = 0; q < kMaxRhs; ++q) {
-    const double bn = q < nrhs ? sqrt(sum_partials(partial, q)) : 0.0;
+  __shared__ int act[kMaxRhs];
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double bn = q < nrhs ? sqrt(sum_partials_warp(partial, q)) : 0.0;
+  if (lane == 0) {
     sc->bnorm[q] = bn;
     sc->rnorm[q] = bn;
     sc->rho[q] = 0.0;
     sc->alpha[q] = 0.0;
     sc->beta[q] = 0.0;
     sc->iters[q] = 0;
-    sc->active[q] = (q < nrhs && bn > 0.0) ? 1 : 0;
-    any |= sc->active[q];
+    act[q] = (q < nrhs && bn > 0.0) ? 1 : 0;
+    sc->active[q] = act[q];
   }
-  sc->first = 1;
-  sc->any_active = any;
-  sc->breakdown = 0;
-  sc->rtol = rtol;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int any = 0;
+    for (int j = 0; j < kMaxRhs; ++j) any |= act[j];
+    sc->first = 1;
+    sc->any_active = any;
+    sc->breakdown = 0;
+    sc->rtol = rtol;
+  }
 }
 
 // rho_new = r.z; beta = rho_new/rho (0 on the first iteration); rho = rho_new
 __global__ void pcg_beta_kernel(PcgScalars* sc, const double* partial, int nrhs) {
-  const int q = threadIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int first = sc->first;
-  __syncwarp();
+  __syncthreads();
   if (q < nrhs) {
-    const double rn = sum_partials(partial, q);
-    double beta = 0.0;
-    if (!first && sc->rho[q] != 0.0) beta = rn / sc->rho[q];
-    if (!isfinite(rn) || !isfinite(beta)) {
-      if (sc->active[q]) sc->breakdown = 1;
-      beta = 0.0;
+    const double rn = sum_partials_warp(partial, q);
+    if (lane == 0) {
+      double beta = 0.0;
+      if (!first && sc->rho[q] != 0.0) beta = rn / sc->rho[q];
+      if (!isfinite(rn) || !isfinite(beta)) {
+        if (sc->active[q]) sc->breakdown = 1;
+        beta = 0.0;
+      }
+      sc->beta[q] = beta;
+      sc->rho[q] = rn;
     }
-    sc->beta[q] = beta;
-    sc->rho[q] = rn;
   }
-  if (q == 0) sc->first = 0;
+  if (threadIdx.x == 0) sc->first = 0;
 }
 
 template <typename TZ>
 __global__ void pcg_p_kernel(const PcgScalars* __restrict__ sc, const TZ* __restrict__ z,
                              double* __restrict__ p, int64_t n, int nrhs) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(e % nrhs);
-    if (sc->active[q]) p[e] = (double)z[e] + sc->beta[q] * p[e];
+  __shared__ double beta[kMaxRhs];
+  __shared__ int act[kMaxRhs];
+  if (threadIdx.x < kMaxRhs) {
+    beta[threadIdx.x] = sc->beta[threadIdx.x];
+    act[threadIdx.x] = sc->active[threadIdx.x];
+  }
+  __syncthreads();
+  const unsigned un = (unsigned)n, ur = (unsigned)nrhs;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < un; e += gridDim.x * blockDim.x) {
+    const unsigned q = e % ur;
+    if (act[q]) p[e] = (double)z[e] + beta[q] * p[e];
   }
 }
 
 // alpha = rho / (p.q); breakdown if p.q <= 0 or non-finite on an active column
 __global__ void pcg_alpha_kernel(PcgScalars* sc, const double* partial, int nrhs) {
-  const int q = threadIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= nrhs) return;
-  const double pq = sum_partials(partial, q);
+  const double pq = sum_partials_warp(partial, q);
+  if (lane != 0) return;
   double alpha = 0.0;
   if (sc->active[q]) {
     if (!(pq > 0.0) || !isfinite(pq)) {
@@ -203,52 +219,57 @@ __global__ void __launch_bounds__(kDotThreads) pcg_update_kernel(
     const PcgScalars* __restrict__ sc, const double* __restrict__ p, double* __restrict__ qv,
     double* __restrict__ x, double* __restrict__ r, double* __restrict__ partial, int64_t rows,
     int nrhs) {
-  double v[kMaxRhs];
-  double al[kMaxRhs];
-#pragma unroll
-  for (int q = 0; q < kMaxRhs; ++q) {
-    v[q] = 0.0;
-    al[q] = q < nrhs ? sc->alpha[q] : 0.0;
-  }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < kMaxRhs; ++q) {
-      if (q < nrhs) {
-        const int64_t e = i * nrhs + q;
-        const double qq = qv[e];
-        x[e] += al[q] * p[e];
-        const double rr = r[e] - al[q] * qq;
-        r[e] = rr;
-        qv[e] = 0.0;
-        v[q] += rr * rr;
-      }
+  const unsigned act = dot_threads(nrhs);
+  const unsigned n = (unsigned)(rows * nrhs);
+  double v = 0.0;
+  if (threadIdx.x < act) {
+    const double al = sc->alpha[threadIdx.x % nrhs];
+    for (unsigned e = blockIdx.x * act + threadIdx.x; e < n; e += gridDim.x * act) {
+      const double qq = qv[e];
+      x[e] += al * p[e];
+      const double rr = r[e] - al * qq;
+      r[e] = rr;
+      qv[e] = 0.0;
+      v += rr * rr;
     }
   }
-  block_reduce_store(v, nrhs, partial);
+  block_store_partials(v, nrhs, partial);
 }
 
 __global__ void pcg_check_kernel(PcgScalars* sc, const double* partial, int nrhs) {
-  if (threadIdx.x != 0) return;
-  int any = 0;
-  for (int q = 0; q < nrhs; ++q) {
-    if (sc->active[q]) {
-      const double rn = sqrt(sum_partials(partial, q));
+  __shared__ int act[kMaxRhs];
+  __shared__ int bad[kMaxRhs];
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double rn = q < nrhs ? sqrt(sum_partials_warp(partial, q)) : 0.0;
+  if (lane == 0) {
+    int a = 0, b = 0;
+    if (q < nrhs && sc->active[q]) {
       sc->rnorm[q] = rn;
       sc->iters[q] += 1;
-      if (rn <= sc->rtol * sc->bnorm[q]) sc->active[q] = 0;
-      if (!isfinite(rn)) sc->breakdown = 1;
+      a = rn <= sc->rtol * sc->bnorm[q] ? 0 : 1;
+      b = isfinite(rn) ? 0 : 1;
+      sc->active[q] = a;
     }
-    any |= sc->active[q];
+    act[q] = a;
+    bad[q] = b;
   }
-  sc->any_active = sc->breakdown ? 0 : any;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int any = 0, brk = 0;
+    for (int j = 0; j < kMaxRhs; ++j) {
+      any |= act[j];
+      brk |= bad[j];
+    }
+    if (brk) sc->breakdown = 1;
+    sc->any_active = sc->breakdown ? 0 : any;
+  }
 }
 
 __global__ void axpby_dinv_kernel(const double* __restrict__ u, const double* __restrict__ dinv,
                                   const double* __restrict__ vprev, double beta,
                                   double* __restrict__ w, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n;
+       e += gridDim.x * blockDim.x)
     w[e] = dinv[e] * u[e] - beta * vprev[e];
 }
 
@@ -256,29 +277,30 @@ __global__ void __launch_bounds__(kDotThreads) dotw_kernel(const double* __restr
                                                            const double* __restrict__ b,
                                                            const double* __restrict__ wgt,
                                                            double* __restrict__ partial, int64_t n) {
-  double v[kMaxRhs];
-#pragma unroll
-  for (int q = 0; q < kMaxRhs; ++q) v[q] = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    v[0] += a[e] * b[e] * wgt[e];
-  block_reduce_store(v, 1, partial);
+  double v = 0.0;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n;
+       e += gridDim.x * blockDim.x)
+    v += a[e] * b[e] * wgt[e];
+  block_store_partials(v, 1, partial);
 }
 
 __global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y,
                             double sy, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n;
+       e += gridDim.x * blockDim.x)
     y[e] = sy * y[e] + a * x[e];
 }
 
 }  // namespace
+
+inline bool too_big(int64_t n) { return n > (int64_t)INT32_MAX; }
 
 template <typename T>
 cudaError_t launch_cheb_init(const T* f, const T* dinv, T* d, T* x, double c, int64_t rows,
                              int nrhs, cudaStream_t s) {
   const int64_t n = rows * nrhs;
   if (n == 0) return cudaSuccess;
+  if (too_big(n)) return cudaErrorInvalidValue;
   cheb_init_kernel<T><<<vblocks(n), 256, 0, s>>>(f, dinv, d, x, (T)c, n, nrhs);
   return cudaGetLastError();
 }
@@ -287,6 +309,7 @@ cudaError_t launch_cheb_step(const T* f, T* t, const T* dinv, T* d, T* x, double
                              int64_t rows, int nrhs, cudaStream_t s) {
   const int64_t n = rows * nrhs;
   if (n == 0) return cudaSuccess;
+  if (too_big(n)) return cudaErrorInvalidValue;
   cheb_step_kernel<T><<<vblocks(n), 256, 0, s>>>(f, t, dinv, d, x, (T)cd, (T)cr, n, nrhs);
   return cudaGetLastError();
 }
@@ -294,68 +317,77 @@ template <typename T>
 cudaError_t launch_residual(const T* f, T* t, T* r, int64_t rows, int nrhs, cudaStream_t s) {
   const int64_t n = rows * nrhs;
   if (n == 0) return cudaSuccess;
+  if (too_big(n)) return cudaErrorInvalidValue;
   residual_kernel<T><<<vblocks(n), 256, 0, s>>>(f, t, r, n);
   return cudaGetLastError();
 }
 template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* a, TO* b, int64_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  if (too_big(n)) return cudaErrorInvalidValue;
   cast_kernel<TI, TO><<<vblocks(n), 256, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
 template <typename TB>
 cudaError_t launch_dot_partial(const double* a, const TB* b, double* partial, int64_t rows,
                                int nrhs, cudaStream_t s) {
+  if (too_big(rows * nrhs)) return cudaErrorInvalidValue;
   dot_kernel<TB><<<kDotBlocks, kDotThreads, 0, s>>>(a, b, partial, rows, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r, double* x,
                             double* p, double* partial, int64_t rows, int nrhs, cudaStream_t s) {
+  if (too_big(rows * nrhs)) return cudaErrorInvalidValue;
   pcg_init_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, row_free, r, x, p, partial, rows, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_start(PcgScalars* sc, const double* partial, int nrhs, double rtol,
                              cudaStream_t s) {
-  pcg_start_kernel<<<1, 32, 0, s>>>(sc, partial, nrhs, rtol);
+  pcg_start_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs, rtol);
   return cudaGetLastError();
 }
 template <typename TZ>
 cudaError_t launch_pcg_beta_p(PcgScalars* sc, const double* partial, const TZ* z, double* p,
                               int64_t rows, int nrhs, cudaStream_t s) {
-  pcg_beta_kernel<<<1, 32, 0, s>>>(sc, partial, nrhs);
+  pcg_beta_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = rows * nrhs;
+  if (too_big(n)) return cudaErrorInvalidValue;
   pcg_p_kernel<TZ><<<vblocks(n), 256, 0, s>>>(sc, z, p, n, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_alpha(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s) {
-  pcg_alpha_kernel<<<1, 32, 0, s>>>(sc, partial, nrhs);
+  pcg_alpha_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_update(const PcgScalars* sc, const double* p, double* q, double* x,
                               double* r, double* partial, int64_t rows, int nrhs, cudaStream_t s) {
+  if (too_big(rows * nrhs)) return cudaErrorInvalidValue;
   pcg_update_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(sc, p, q, x, r, partial, rows, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s) {
-  pcg_check_kernel<<<1, 32, 0, s>>>(sc, partial, nrhs);
+  pcg_check_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_axpby_dinv(const double* u, const double* dinv, const double* vprev,
                               double beta, double* w, int64_t rows, cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
+  if (too_big(rows)) return cudaErrorInvalidValue;
   axpby_dinv_kernel<<<vblocks(rows), 256, 0, s>>>(u, dinv, vprev, beta, w, rows);
   return cudaGetLastError();
 }
 cudaError_t launch_dot_weighted(const double* a, const double* b, const double* wgt,
                                 double* partial, int64_t rows, cudaStream_t s) {
+  if (too_big(rows)) return cudaErrorInvalidValue;
   dotw_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, wgt, partial, rows);
   return cudaGetLastError();
 }
 cudaError_t launch_axpy(double a, const double* x, double* y, double sy, int64_t rows,
                         cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
+  if (too_big(rows)) return cudaErrorInvalidValue;
   axpy_kernel<<<vblocks(rows), 256, 0, s>>>(a, x, y, sy, rows);
   return cudaGetLastError();
 }
