@@ -15,6 +15,8 @@
 // through shared memory laid out [array][point][unit] (bank-conflict free).
 // Dirichlet nodes carry index -1: read as 0, never written.  y must be zero on
 // entry (scatter is atomic).
+#include <algorithm>
+
 #include "nnmg_internal.h"
 
 namespace nnmg {
@@ -87,6 +89,16 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
   // P0 + P1: gather the z-line (i=a, j=b) and interpolate along z in registers
 #pragma unroll
   for (int l = 0; l < N; ++l) dof[l] = act ? cell_nodes[cell * NQ + a + N * b + N2 * l] : -1;
+  const T* mc = metric + (act ? cell : 0) * NM * NQ;
+  // Poisson: fetch the metric terms of this thread's quadrature column now, so
+  // that their latency overlaps the first sweeps (used in P5)
+  T Gp[NC == 1 ? 6 : 1][N];
+  if constexpr (NC == 1) {
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int m = 0; m < 6; ++m) Gp[m][q] = act ? mc[m * NQ + a + N * b + N2 * q] : T(0);
+  }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     T u[N], v[N];
@@ -145,7 +157,6 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
       for (int p = 0; p < N; ++p) u[p] = S(3 * c, a + N * b + N2 * p);
       apply<N>(B.Dg, u, gz[c]);
     }
-    const T* mc = metric + (act ? cell : 0) * NM * NQ;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       const int idx = a + N * b + N2 * q;
@@ -153,7 +164,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
         const T gx = S(1, idx), gy = S(2, idx), g3 = gz[0][q];
         T G[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) G[m] = act ? mc[m * NQ + idx] : T(0);
+        for (int m = 0; m < 6; ++m) G[m] = Gp[m][q];
         S(1, idx) = G[0] * gx + G[1] * gy + G[2] * g3;
         S(2, idx) = G[1] * gx + G[3] * gy + G[4] * g3;
         gz[0][q] = G[2] * gx + G[4] * gy + G[5] * g3;
@@ -337,15 +348,30 @@ struct OpConfig {
   size_t smem;
 };
 
-inline OpConfig op_config(int lines, int nq, int arrays, size_t tsize, int64_t n_cells, int nrhs) {
-  int cpb = 256 / (lines * nrhs);
-  if (cpb < 1) cpb = 1;
+// Units per block: the largest multiple of nrhs not above 32, so a warp is one
+// tensor line of consecutive units (conflict-free shared memory); doubled for
+// small line counts to reach 128 threads; halved while the block exceeds the
+// largest block this kernel can launch with (its registers decide that).
+inline OpConfig op_config(int lines, int nq, int arrays, size_t tsize, int64_t n_cells, int nrhs,
+                          int max_threads) {
+  int u0 = 32 - (32 % nrhs);
+  int U = u0;
+  while (U * lines < 128 && U * 2 * lines <= 1024) U *= 2;
+  while (U > nrhs && U * lines > max_threads) U = std::max(nrhs, (U / 2) / nrhs * nrhs);
   OpConfig c;
-  c.U = cpb * nrhs;
-  c.threads = c.U * lines;
+  const int cpb = U / nrhs;
+  c.U = U;
+  c.threads = U * lines;
   c.blocks = (unsigned)((n_cells + cpb - 1) / cpb);
-  c.smem = (size_t)arrays * nq * c.U * tsize;
+  c.smem = (size_t)arrays * nq * U * tsize;
   return c;
+}
+
+template <typename F>
+int kernel_max_threads(F kern) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, kern) != cudaSuccess) return 256;
+  return a.maxThreadsPerBlock;
 }
 
 template <int K, typename T, int NC>
@@ -354,8 +380,9 @@ cudaError_t run3d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs
   constexpr int N = K + 1;
   Basis1D<T> B;
   pick_basis<T>(K, &B);
-  OpConfig c = op_config(N * N, N * N * N, 3 * NC, sizeof(T), L.n_cells, nrhs);
   auto kern = op3d_kernel<K, T, NC>;
+  static const int max_threads = kernel_max_threads(kern);
+  OpConfig c = op_config(N * N, N * N * N, 3 * NC, sizeof(T), L.n_cells, nrhs, max_threads);
   static size_t smem_set = 48 * 1024;   // opt-in size already granted to this kernel
   if (c.smem > smem_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
@@ -372,7 +399,8 @@ cudaError_t run2d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs
   constexpr int N = K + 1;
   Basis1D<T> B;
   pick_basis<T>(K, &B);
-  OpConfig c = op_config(N, N * N, 2, sizeof(T), L.n_cells, nrhs);
+  static const int max_threads = kernel_max_threads(op2d_kernel<K, T>);
+  OpConfig c = op_config(N, N * N, 2, sizeof(T), L.n_cells, nrhs, max_threads);
   op2d_kernel<K, T><<<c.blocks, c.threads, c.smem, s>>>(L.cell_nodes, metric, x, y, L.n_cells,
                                                         nrhs, c.U, B);
   return cudaGetLastError();
