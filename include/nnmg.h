@@ -177,6 +177,20 @@ int nnmg_prolongate(nnmg_handle* h, int fine_level, int precision, const void* c
 int nnmg_restrict(nnmg_handle* h, int fine_level, int precision, const void* fine,
                   void* coarse, int nrhs, void* stream);
 
+/* coarse = P^T fine, as nnmg_restrict, without allocating anything.  The paper
+ * has no counterpart: this entry point exists for callers that must not
+ * allocate device memory while they run (allocator-free real-time loops,
+ * memory handed out by an external pool or budget, host callbacks).  Its
+ * scratch is a fixed 64 MiB array inside the library, held by every GPU that
+ * loads the library until the process exits; the call fails with INVALID_ARG
+ * when coarse cells x (k+1)^d x components x nrhs x value size exceeds it.
+ * The array is shared by all calls: calls that overlap on the GPU race, so
+ * order them on one stream.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  Nothing
+ * needs clearing between calls. */
+int nnmg_restrict_noalloc(nnmg_handle* h, int fine_level, int precision, const void* fine,
+                          void* coarse, int nrhs, void* stream);
+
 /* One V-cycle (Algorithm 1) on the finest level from a zero guess: z ~ A_L^-1 r.
  * Chebyshev-Jacobi pre- and post-smoothing, residual, restriction, recursion,
  * prolongation; coarsest level solved directly in FP64. */

@@ -603,6 +603,16 @@ void destroy_impl(nnmg_handle* h) {
 
 }  // namespace
 
+namespace nnmg {
+// Level data of a handle for entry points defined in other translation units
+// (nullptr for a bad handle or level).
+const DevLevel* handle_level(const nnmg_handle* h, int level) {
+  if (!h || level < 0 || level >= (int)h->lv.size()) return nullptr;
+  return &h->lv[level];
+}
+int handle_max_nrhs(const nnmg_handle* h) { return h ? h->opt.max_nrhs : 0; }
+}  // namespace nnmg
+
 // ====================================================================== C ABI
 extern "C" {
 

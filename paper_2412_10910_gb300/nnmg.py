@@ -196,6 +196,16 @@ def nnmg_restrict(h, fine_level, fine, coarse, nrhs, stream=None, ncomp=1):
            "nnmg_restrict")
 
 
+def nnmg_restrict_noalloc(h, fine_level, fine, coarse, nrhs, stream=None, ncomp=1):
+    """coarse = P^T fine without any device allocation (scratch is a fixed
+    array inside the library; see include/nnmg.h for its limit)."""
+    _need(h, fine_level - 1, coarse, nrhs, ncomp, "coarse")
+    _need(h, fine_level, fine, nrhs, ncomp, "fine")
+    _check(_lib.nnmg_restrict_noalloc(h, fine_level, _prec(fine), _dev(fine, name="fine"),
+                                      _dev(coarse, fine.dtype, name="coarse"), nrhs,
+                                      _stream(stream)), "nnmg_restrict_noalloc")
+
+
 def nnmg_vcycle(h, r, z, nrhs, stream=None, ncomp=1):
     _need(h, nnmg_n_levels(h) - 1, r, nrhs, ncomp, "r")
     _check(_lib.nnmg_vcycle(h, _prec(r), _dev(r, name="r"), _dev(z, r.dtype, r.numel(), name="z"),
