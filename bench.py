@@ -37,6 +37,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 CUDA-core peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
+# fine-level operator on this workload (404.6 + 66.0 MB).
+OP64_TRAFFIC_BYTES = 470.7e6
 
 
 def _peaks():
@@ -178,6 +181,54 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, rank):
+    """Serving mix: 12 cached mesh families, Poisson arrivals, continuous batching."""
+    import torch
+    from paper_2412_10910_gb300.serving import FamilySpec, Request, Server, latency_stats
+    from synthetic.serving import request_rhs, serving_families, serving_requests
+
+    fams = serving_families()
+    specs = {f["name"]: FamilySpec(f["levels"], f["degree"]) for f in fams}
+    budget = int(0.5 * torch.cuda.get_device_properties(0).total_memory)
+    server = Server(specs, budget_bytes=budget)
+    t = time.perf_counter()
+    server.prepare([f["name"] for f in fams])
+    setup_s = time.perf_counter() - t
+
+    def make(reqs):
+        out = []
+        for rid, (fi, m, arr) in enumerate(reqs):
+            f = fams[fi]
+            out.append(Request(rid, f["name"], request_rhs(f["n_nodes"], m, rid), arrival=arr))
+        return out
+
+    # calibration: a closed burst (all requests at t = 0) gives the service rate
+    ncal = max(24, args.requests // 20)
+    cal = make(serving_requests(fams, ncal, seed=7, rate=1e9))
+    t = time.perf_counter()
+    server.run(cal)
+    cal_rate = ncal / (time.perf_counter() - t)
+    rate = 0.8 * cal_rate
+    reqs = make(serving_requests(fams, args.requests, seed=6, rate=rate))
+    t = time.perf_counter()
+    done = server.run(reqs)
+    span = time.perf_counter() - t
+    dofs = sum(next(f for f in fams if f["name"] == r.family)["n_free"] * r.nrhs for r in done)
+    ok = all(all(s == 0 for s in r.status) and max(r.relres) <= 1e-8 for r in done)
+    line = {"metric": "serving: solved DoF/s and p50/p99 request latency", "value": dofs / span,
+            "unit": UNIT, "requests": len(done), "arrival_rate_per_s": rate,
+            "calibration_rate_per_s": cal_rate, "makespan_s": span,
+            "latency": latency_stats(done), "all_converged": ok, "setup_s_12_families": setup_s,
+            "evictions": server.evictions, "budget_bytes": budget,
+            "families": [f["name"] for f in fams], "data": "synthetic",
+            "config": {"workload": "serving mix: 12 jittered non-nested families (seed 5), "
+                                   "Poisson arrivals (seed 6), 1-16 N(0,1) RHS, FP32 V-cycle / "
+                                   "FP64 CG to 1e-8, continuous batching over 16 slots per family"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    server.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,8 +236,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["solve", "solve64", "vcycle", "op64", "op32"], default=None,
-                    help="run only one timed section (for profiler launch lists)")
+    ap.add_argument("--only", choices=["solve", "solve64", "vcycle", "op64", "op32", "serving"],
+                    default=None, help="run only one timed section (for profiler launch lists), "
+                    "or the serving mix")
+    ap.add_argument("--requests", type=int, default=2000, help="serving mix: number of requests")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -203,6 +256,8 @@ def main():
     from synthetic.meshes import CONFIGS
 
     torch.cuda.set_device(local)
+    if args.only == "serving":
+        return run_serving(args, rank)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
@@ -249,10 +304,12 @@ def main():
             fn()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")      # profilers select this range
         e0.record(stream)
         for _ in range(args.steps):
             fn()
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         barrier()
         if rank == 0:
             print(json.dumps({"only": args.only, "ms_per_step": e0.elapsed_time(e1) / args.steps}))
@@ -354,7 +411,10 @@ def main():
                            "f64": n_nodes * nrhs / (op64_ms / 1e3) / 1e9},
         "roofline": {"kernel": "op3d_kernel<2,double,1> (FP64 fine-level operator, 8 RHS)",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     # DRAM bytes read + written per launch, ncu capture of this kernel
+                     # (profiles/op3d_f64_q2_c2_fine_8rhs.md)
+                     "traffic": OP64_TRAFFIC_BYTES,
                      "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
         "e2e": {"value": dofs * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": rows * nrhs * 8, "d2h_bytes_per_step": rows * nrhs * 8},

@@ -212,6 +212,32 @@ int nnmg_pcg_solve_host(nnmg_handle* h, int mode, const double* b_host, double* 
                         int nrhs, double rtol, int maxit, int* iters_out,
                         double* relres_out, void* stream);
 
+/* Continuous batching (serving).  The PCG of nnmg_pcg_solve runs over
+ * `nslots` independent columns; columns can be started and emptied between
+ * iterations while the others continue, so requests that arrive while the GPU
+ * works on earlier ones join the running solve as slots free up.  A column's
+ * arithmetic does not depend on the other columns.  All calls of one handle
+ * must use the same stream; different handles may run on different streams
+ * concurrently.
+ * nnmg_batch_reset: empty all nslots (<= max_nrhs) columns; mode, rtol (per
+ *   column ||r|| <= rtol ||b||) and maxit (per column) as for nnmg_pcg_solve.
+ * nnmg_batch_admit: start column `slot` from the FP64 right-hand side b [rows]
+ *   (device, or host if b_on_host) with x0 = 0.
+ * nnmg_batch_step: enqueue one PCG iteration of all columns (inactive columns
+ *   stay frozen) and an asynchronous copy of the per-column state.
+ * nnmg_batch_poll: if the last step has finished (or, with wait != 0, after
+ *   waiting for it) set *ready = 1 and fill host arrays [nslots] (may be
+ *   NULL): active flags, iteration counts, relative residuals and per-column
+ *   status (NNMG_OK, NNMG_NOT_CONVERGED, NNMG_BREAKDOWN); else *ready = 0.
+ * nnmg_batch_retire: copy column `slot` of x into x [rows] (device, or host if
+ *   x_on_host, then synchronising the stream) and mark the slot empty. */
+int nnmg_batch_reset(nnmg_handle* h, int mode, int nslots, double rtol, int maxit, void* stream);
+int nnmg_batch_admit(nnmg_handle* h, int slot, const double* b, int b_on_host, void* stream);
+int nnmg_batch_step(nnmg_handle* h, void* stream);
+int nnmg_batch_poll(nnmg_handle* h, int wait, int* ready, int* active, int* iters,
+                    double* relres, int* status);
+int nnmg_batch_retire(nnmg_handle* h, int slot, double* x, int x_on_host, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* nnmg_last_error(void);
 

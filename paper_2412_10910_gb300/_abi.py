@@ -56,6 +56,12 @@ PROTOTYPES = {
     "nnmg_pcg_solve_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                       C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    "nnmg_batch_reset": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p]),
+    "nnmg_batch_admit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    "nnmg_batch_step": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nnmg_batch_poll": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+    "nnmg_batch_retire": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_last_error": (C.c_char_p, []),
 }
 

@@ -328,6 +328,120 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
   }
 }
 
+
+// Register-resident variant for small cells (3D k <= 2, 2D k <= 4, Poisson):
+// one thread per (cell, right-hand side) unit keeps all (k+1)^d values, the
+// reference gradients and the fluxes in registers, so the sweeps need no
+// shared memory and no barriers.  Consecutive threads are consecutive units
+// (right-hand side fastest), so a warp's gathers of one local node cover
+// whole 32-byte rows of right-hand sides.
+template <int D, int N, typename T>
+__device__ __forceinline__ void sweep(const T (&M)[kMaxN][kMaxN], T* v, int dir, bool transpose) {
+  // apply M (or M^T) along direction dir to every line of the N^D array v
+  constexpr int NQ = D == 2 ? N * N : N * N * N;
+  const int stride = dir == 0 ? 1 : (dir == 1 ? N : N * N);
+#pragma unroll
+  for (int base = 0; base < NQ; ++base) {
+    const int coord = (base / stride) % N;
+    if (coord != 0) continue;
+    T in[N], out[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) in[i] = v[base + i * stride];
+    if (transpose)
+      apply_t<N>(M, in, out);
+    else
+      apply<N>(M, in, out);
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[base + i * stride] = out[i];
+  }
+}
+
+template <int D, int N, typename T>
+__device__ __forceinline__ void sweep_add_t(const T (&M)[kMaxN][kMaxN], const T* f, T* w, int dir) {
+  // w += M^T applied along dir to f
+  constexpr int NQ = D == 2 ? N * N : N * N * N;
+  const int stride = dir == 0 ? 1 : (dir == 1 ? N : N * N);
+#pragma unroll
+  for (int base = 0; base < NQ; ++base) {
+    const int coord = (base / stride) % N;
+    if (coord != 0) continue;
+    T in[N], out[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) in[i] = f[base + i * stride];
+    apply_t<N>(M, in, out);
+#pragma unroll
+    for (int i = 0; i < N; ++i) w[base + i * stride] += out[i];
+  }
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__ cell_nodes,
+                                                     const T* __restrict__ metric,
+                                                     const T* __restrict__ x, T* __restrict__ y,
+                                                     int64_t n_cells, int nrhs, Basis1D<T> B) {
+  constexpr int N = K + 1;
+  constexpr int NQ = D == 2 ? N * N : N * N * N;
+  constexpr int NM = D == 2 ? 3 : 6;
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cell = u / nrhs;
+  if (cell >= n_cells) return;
+  const int rhs = (int)(u - cell * nrhs);
+  const int32_t* cn = cell_nodes + cell * NQ;
+  T v[NQ], gx[NQ], gy[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int dof = cn[i];
+    v[i] = dof >= 0 ? x[(int64_t)dof * nrhs + rhs] : T(0);
+  }
+  // values at the Gauss points, then collocation derivatives
+#pragma unroll
+  for (int d = 0; d < D; ++d) sweep<D, N, T>(B.S, v, d, false);
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    gx[i] = v[i];
+    gy[i] = v[i];
+  }
+  sweep<D, N, T>(B.Dg, gx, 0, false);
+  sweep<D, N, T>(B.Dg, gy, 1, false);
+  if constexpr (D == 3) sweep<D, N, T>(B.Dg, v, 2, false);  // v now holds d/dz
+  // metric terms: flux = G grad^
+  const T* mc = metric + cell * NM * NQ;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if constexpr (D == 3) {
+      const T a = gx[q], b = gy[q], c = v[q];
+      const T G0 = mc[q], G1 = mc[NQ + q], G2 = mc[2 * NQ + q], G3 = mc[3 * NQ + q],
+              G4 = mc[4 * NQ + q], G5 = mc[5 * NQ + q];
+      gx[q] = G0 * a + G1 * b + G2 * c;
+      gy[q] = G1 * a + G3 * b + G4 * c;
+      v[q] = G2 * a + G4 * b + G5 * c;
+    } else {
+      const T a = gx[q], b = gy[q];
+      const T G0 = mc[q], G1 = mc[NQ + q], G2 = mc[2 * NQ + q];
+      gx[q] = G0 * a + G1 * b;
+      gy[q] = G1 * a + G2 * b;
+    }
+  }
+  // w = Dx^T fx + Dy^T fy (+ Dz^T fz), then integrate with S^T
+  if constexpr (D == 3) {
+    sweep<D, N, T>(B.Dg, v, 2, true);
+    sweep_add_t<D, N, T>(B.Dg, gy, v, 1);
+    sweep_add_t<D, N, T>(B.Dg, gx, v, 0);
+  } else {
+    sweep<D, N, T>(B.Dg, gy, 1, true);
+    sweep_add_t<D, N, T>(B.Dg, gx, gy, 0);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) v[i] = gy[i];
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) sweep<D, N, T>(B.S, v, d, true);
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int dof = cn[i];
+    if (dof >= 0) atomicAdd(&y[(int64_t)dof * nrhs + rhs], v[i]);
+  }
+}
+
 template <typename T>
 void pick_basis(int k, Basis1D<T>* b);
 template <>
@@ -352,12 +466,18 @@ struct OpConfig {
 // tensor line of consecutive units (conflict-free shared memory); doubled for
 // small line counts to reach 128 threads; halved while the block exceeds the
 // largest block this kernel can launch with (its registers decide that).
+constexpr size_t kMaxSmem = 227 * 1024;
+
 inline OpConfig op_config(int lines, int nq, int arrays, size_t tsize, int64_t n_cells, int nrhs,
-                          int max_threads) {
+                          int max_threads, int units) {
+  const size_t per_unit = (size_t)arrays * nq * tsize;
   int u0 = 32 - (32 % nrhs);
   int U = u0;
   while (U * lines < 128 && U * 2 * lines <= 1024) U *= 2;
-  while (U > nrhs && U * lines > max_threads) U = std::max(nrhs, (U / 2) / nrhs * nrhs);
+  while (U > nrhs && (U * lines > max_threads || U * per_unit > kMaxSmem))
+    U = std::max(nrhs, (U / 2) / nrhs * nrhs);
+  if (units > 0 && units % nrhs == 0 && units * lines <= max_threads && units * per_unit <= kMaxSmem)
+    U = units;
   OpConfig c;
   const int cpb = U / nrhs;
   c.U = U;
@@ -374,15 +494,28 @@ int kernel_max_threads(F kern) {
   return a.maxThreadsPerBlock;
 }
 
+// Candidate units per block: multiples of nrhs from nrhs up to the kernel's
+// largest block, doubling from the warp-aligned default.
+inline int unit_candidates(int lines, int nrhs, int max_threads, size_t per_unit, int* out,
+                           int max_out) {
+  int n = 0;
+  int u0 = 32 - (32 % nrhs);
+  for (int U = std::max(nrhs, u0 / 4 / nrhs * nrhs);
+       U * lines <= max_threads && U * per_unit <= kMaxSmem && n < max_out; U *= 2)
+    if (U * lines >= 32) out[n++] = U;
+  if (n == 0 && n < max_out) out[n++] = nrhs;
+  return n;
+}
+
 template <int K, typename T, int NC>
 cudaError_t run3d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs, double lambda,
-                  double mu, cudaStream_t s) {
+                  double mu, cudaStream_t s, int units) {
   constexpr int N = K + 1;
   Basis1D<T> B;
   pick_basis<T>(K, &B);
   auto kern = op3d_kernel<K, T, NC>;
   static const int max_threads = kernel_max_threads(kern);
-  OpConfig c = op_config(N * N, N * N * N, 3 * NC, sizeof(T), L.n_cells, nrhs, max_threads);
+  OpConfig c = op_config(N * N, N * N * N, 3 * NC, sizeof(T), L.n_cells, nrhs, max_threads, units);
   static size_t smem_set = 48 * 1024;   // opt-in size already granted to this kernel
   if (c.smem > smem_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
@@ -395,12 +528,13 @@ cudaError_t run3d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs
 }
 
 template <int K, typename T>
-cudaError_t run2d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs, cudaStream_t s) {
+cudaError_t run2d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs, cudaStream_t s,
+                  int units) {
   constexpr int N = K + 1;
   Basis1D<T> B;
   pick_basis<T>(K, &B);
   static const int max_threads = kernel_max_threads(op2d_kernel<K, T>);
-  OpConfig c = op_config(N, N * N, 2, sizeof(T), L.n_cells, nrhs, max_threads);
+  OpConfig c = op_config(N, N * N, 2, sizeof(T), L.n_cells, nrhs, max_threads, units);
   op2d_kernel<K, T><<<c.blocks, c.threads, c.smem, s>>>(L.cell_nodes, metric, x, y, L.n_cells,
                                                         nrhs, c.U, B);
   return cudaGetLastError();
@@ -415,39 +549,87 @@ const float* metric_of<float>(const DevLevel& L) { return L.metric32; }
 
 }  // namespace
 
+template <int D, int K, typename T>
+cudaError_t run_reg(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs,
+                    cudaStream_t s) {
+  Basis1D<T> B;
+  pick_basis<T>(K, &B);
+  const int64_t units = L.n_cells * nrhs;
+  op_reg_kernel<D, K, T><<<(unsigned)((units + 127) / 128), 128, 0, s>>>(L.cell_nodes, metric, x, y,
+                                                                         L.n_cells, nrhs, B);
+  return cudaGetLastError();
+}
+
+// The register-resident kernel serves FP32 Poisson cells with at most 27
+// (3D) or 25 (2D) nodes; units < 0 asks for it explicitly, units > 0 for the
+// shared-memory kernel with that many units per block (autotuner choices).
+template <typename T>
+bool reg_eligible(const DevLevel& L) {
+  return sizeof(T) == 4 && L.ncomp == 1 && (L.dim == 2 || L.k <= 2);
+}
+
 template <typename T>
 cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, double lambda,
-                            double mu, cudaStream_t s) {
+                            double mu, cudaStream_t s, int units) {
   if (L.n_cells == 0) return cudaSuccess;
   const T* m = metric_of<T>(L);
+  if constexpr (sizeof(T) == 4) {
+    if (reg_eligible<T>(L) && units <= 0) {
+#define NNMG_REG(D, K) if (L.dim == D && L.k == K) return run_reg<D, K, T>(L, m, x, y, nrhs, s);
+      NNMG_REG(2, 1) NNMG_REG(2, 2) NNMG_REG(2, 3) NNMG_REG(2, 4) NNMG_REG(3, 1) NNMG_REG(3, 2)
+#undef NNMG_REG
+    }
+  }
   if (L.dim == 2) {
     switch (L.k) {
-      case 1: return run2d<1, T>(L, m, x, y, nrhs, s);
-      case 2: return run2d<2, T>(L, m, x, y, nrhs, s);
-      case 3: return run2d<3, T>(L, m, x, y, nrhs, s);
-      case 4: return run2d<4, T>(L, m, x, y, nrhs, s);
+      case 1: return run2d<1, T>(L, m, x, y, nrhs, s, units);
+      case 2: return run2d<2, T>(L, m, x, y, nrhs, s, units);
+      case 3: return run2d<3, T>(L, m, x, y, nrhs, s, units);
+      case 4: return run2d<4, T>(L, m, x, y, nrhs, s, units);
     }
   } else if (L.ncomp == 1) {
     switch (L.k) {
-      case 1: return run3d<1, T, 1>(L, m, x, y, nrhs, lambda, mu, s);
-      case 2: return run3d<2, T, 1>(L, m, x, y, nrhs, lambda, mu, s);
-      case 3: return run3d<3, T, 1>(L, m, x, y, nrhs, lambda, mu, s);
-      case 4: return run3d<4, T, 1>(L, m, x, y, nrhs, lambda, mu, s);
+      case 1: return run3d<1, T, 1>(L, m, x, y, nrhs, lambda, mu, s, units);
+      case 2: return run3d<2, T, 1>(L, m, x, y, nrhs, lambda, mu, s, units);
+      case 3: return run3d<3, T, 1>(L, m, x, y, nrhs, lambda, mu, s, units);
+      case 4: return run3d<4, T, 1>(L, m, x, y, nrhs, lambda, mu, s, units);
     }
   } else {
     switch (L.k) {
-      case 1: return run3d<1, T, 3>(L, m, x, y, nrhs, lambda, mu, s);
-      case 2: return run3d<2, T, 3>(L, m, x, y, nrhs, lambda, mu, s);
-      case 3: return run3d<3, T, 3>(L, m, x, y, nrhs, lambda, mu, s);
-      case 4: return run3d<4, T, 3>(L, m, x, y, nrhs, lambda, mu, s);
+      case 1: return run3d<1, T, 3>(L, m, x, y, nrhs, lambda, mu, s, units);
+      case 2: return run3d<2, T, 3>(L, m, x, y, nrhs, lambda, mu, s, units);
+      case 3: return run3d<3, T, 3>(L, m, x, y, nrhs, lambda, mu, s, units);
+      case 4: return run3d<4, T, 3>(L, m, x, y, nrhs, lambda, mu, s, units);
     }
   }
   return cudaErrorInvalidValue;
 }
 
+template <typename T>
+int operator_unit_candidates(const DevLevel& L, int nrhs, int* out, int max_out) {
+  int lines = 0, mt = 256;
+  size_t per_unit = 0;
+#define NNMG_C(D, K, NC)                                                              \
+  if (L.dim == D && L.k == K && L.ncomp == NC) {                                      \
+    lines = D == 2 ? K + 1 : (K + 1) * (K + 1);                                       \
+    per_unit = (D == 2 ? 2 : 3 * NC) * (size_t)lines * (K + 1) * sizeof(T);          \
+    mt = D == 2 ? kernel_max_threads(op2d_kernel<K, T>) : kernel_max_threads(op3d_kernel<K, T, NC>); \
+  }
+  NNMG_C(2, 1, 1) NNMG_C(2, 2, 1) NNMG_C(2, 3, 1) NNMG_C(2, 4, 1)
+  NNMG_C(3, 1, 1) NNMG_C(3, 2, 1) NNMG_C(3, 3, 1) NNMG_C(3, 4, 1)
+  NNMG_C(3, 1, 3) NNMG_C(3, 2, 3) NNMG_C(3, 3, 3) NNMG_C(3, 4, 3)
+#undef NNMG_C
+  if (lines == 0) return 0;
+  int n = 0;
+  if (reg_eligible<T>(L) && max_out > 0) out[n++] = -1;   // the register-resident kernel
+  return n + unit_candidates(lines, nrhs, mt, per_unit, out + n, max_out - n);
+}
+
 template cudaError_t launch_operator<float>(const DevLevel&, const float*, float*, int, double,
-                                            double, cudaStream_t);
+                                            double, cudaStream_t, int);
 template cudaError_t launch_operator<double>(const DevLevel&, const double*, double*, int, double,
-                                             double, cudaStream_t);
+                                             double, cudaStream_t, int);
+template int operator_unit_candidates<float>(const DevLevel&, int, int*, int);
+template int operator_unit_candidates<double>(const DevLevel&, int, int*, int);
 
 }  // namespace nnmg

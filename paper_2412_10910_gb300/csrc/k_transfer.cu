@@ -14,6 +14,8 @@
 // cell-local buffer; (2) per coarse node, the buffer entries of the cells that
 // share it are summed in ascending (cell, local) order.  No atomics: results
 // are bitwise reproducible.
+#include <algorithm>
+
 #include "nnmg_internal.h"
 
 namespace nnmg {
@@ -145,18 +147,23 @@ __global__ void restrict2_kernel(const T* __restrict__ buf, const int32_t* __res
 constexpr int kCoarseRows = 8;
 constexpr int kCoarseTile = 256;
 
+// The column range of every row is split over gridDim.y segments; segment s
+// writes partial[s][row][rhs] and coarse_sum_kernel adds the segments in order
+// (deterministic).  With gridDim.y == 1 the kernel writes z directly.
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(32 * kCoarseRows) coarse_solve_kernel(
     const double* __restrict__ Ainv, const int32_t* __restrict__ rows, int n,
-    const TI* __restrict__ r, TO* __restrict__ z, int nrhs) {
+    const TI* __restrict__ r, TO* __restrict__ z, int nrhs, double* __restrict__ partial) {
   __shared__ double sr[kMaxRhs * kCoarseTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kCoarseRows + warp;
+  const int seg = (n + gridDim.y - 1) / gridDim.y;
+  const int jb = blockIdx.y * seg, je = min(n, jb + seg);
   double acc[kMaxRhs];
 #pragma unroll
   for (int q = 0; q < kMaxRhs; ++q) acc[q] = 0.0;
-  for (int j0 = 0; j0 < n; j0 += kCoarseTile) {
-    const int nt = min(kCoarseTile, n - j0);
+  for (int j0 = jb; j0 < je; j0 += kCoarseTile) {
+    const int nt = min(kCoarseTile, je - j0);
     for (int t = threadIdx.x; t < nt * nrhs; t += blockDim.x) {
       const int jj = t / nrhs, q = t - jj * nrhs;
       sr[q * kCoarseTile + jj] = (double)r[(int64_t)rows[j0 + jj] * nrhs + q];
@@ -184,9 +191,25 @@ __global__ void __launch_bounds__(32 * kCoarseRows) coarse_solve_kernel(
     }
   }
   if (lane == 0) {
-    const int64_t ri = (int64_t)rows[i] * nrhs;
-    for (int q = 0; q < nrhs; ++q) z[ri + q] = (TO)acc[q];
+    if (gridDim.y == 1) {
+      const int64_t ri = (int64_t)rows[i] * nrhs;
+      for (int q = 0; q < nrhs; ++q) z[ri + q] = (TO)acc[q];
+    } else {
+      double* pp = partial + ((int64_t)blockIdx.y * n + i) * kMaxRhs;
+      for (int q = 0; q < nrhs; ++q) pp[q] = acc[q];
+    }
   }
+}
+
+template <typename TO>
+__global__ void coarse_sum_kernel(const double* __restrict__ partial, const int32_t* __restrict__ rows,
+                                  int n, int nseg, TO* __restrict__ z, int nrhs) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * nrhs) return;
+  const int i = e / nrhs, q = e - i * nrhs;
+  double s = 0.0;
+  for (int g = 0; g < nseg; ++g) s += partial[((int64_t)g * n + i) * kMaxRhs + q];
+  z[(int64_t)rows[i] * nrhs + q] = (TO)s;
 }
 
 template <typename T>
@@ -279,9 +302,18 @@ cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const 
 template <typename TI, typename TO>
 cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs, cudaStream_t s) {
   if (L.n_free_rows == 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((L.n_free_rows + kCoarseRows - 1) / kCoarseRows);
-  coarse_solve_kernel<TI, TO><<<blocks, 32 * kCoarseRows, 0, s>>>(
-      L.coarse_inv, L.free_rows, L.n_free_rows, r, z, nrhs);
+  const int n = L.n_free_rows;
+  const unsigned blocks = (unsigned)((n + kCoarseRows - 1) / kCoarseRows);
+  // enough segments for ~4 blocks per SM, each segment at least one tile long
+  int nseg = (int)std::min<int64_t>(kCoarseMaxSegments, std::max<int64_t>(1, (4 * 152) / blocks));
+  nseg = std::max(1, std::min(nseg, (n + kCoarseTile - 1) / kCoarseTile));
+  if (!L.coarse_partial) nseg = 1;
+  coarse_solve_kernel<TI, TO><<<dim3(blocks, nseg), 32 * kCoarseRows, 0, s>>>(
+      L.coarse_inv, L.free_rows, n, r, z, nrhs, L.coarse_partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || nseg == 1) return e;
+  coarse_sum_kernel<TO><<<(n * nrhs + 255) / 256, 256, 0, s>>>(L.coarse_partial, L.free_rows, n,
+                                                               nseg, z, nrhs);
   return cudaGetLastError();
 }
 

@@ -132,50 +132,95 @@ __device__ __forceinline__ double sum_partials_warp(const double* partial, int q
 }
 
 // Scalar kernels run one warp per column (blockDim = 32 * kMaxRhs).
-__global__ void pcg_start_kernel(PcgScalars* sc, const double* partial, int nrhs, double rtol) {
+__device__ __forceinline__ void start_column(PcgScalars* sc, int q, double bn, bool used) {
+  sc->bnorm[q] = bn;
+  sc->rnorm[q] = bn;
+  sc->rho[q] = 0.0;
+  sc->alpha[q] = 0.0;
+  sc->beta[q] = 0.0;
+  sc->iters[q] = 0;
+  sc->first[q] = 1;
+  sc->failed[q] = 0;
+  sc->broken[q] = 0;
+  sc->active[q] = (used && bn > 0.0) ? 1 : 0;
+}
+
+__global__ void pcg_start_kernel(PcgScalars* sc, const double* partial, int nrhs, double rtol,
+                                 int maxit) {
   __shared__ int act[kMaxRhs];
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double bn = q < nrhs ? sqrt(sum_partials_warp(partial, q)) : 0.0;
   if (lane == 0) {
-    sc->bnorm[q] = bn;
-    sc->rnorm[q] = bn;
-    sc->rho[q] = 0.0;
-    sc->alpha[q] = 0.0;
-    sc->beta[q] = 0.0;
-    sc->iters[q] = 0;
-    act[q] = (q < nrhs && bn > 0.0) ? 1 : 0;
-    sc->active[q] = act[q];
+    start_column(sc, q, bn, q < nrhs);
+    act[q] = sc->active[q];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     int any = 0;
     for (int j = 0; j < kMaxRhs; ++j) any |= act[j];
-    sc->first = 1;
     sc->any_active = any;
     sc->breakdown = 0;
     sc->rtol = rtol;
+    sc->maxit = maxit;
+  }
+}
+
+__global__ void batch_reset_kernel(PcgScalars* sc, double rtol, int maxit) {
+  const int q = threadIdx.x;
+  if (q < kMaxRhs) start_column(sc, q, 0.0, false);
+  if (q == 0) {
+    sc->any_active = 0;
+    sc->breakdown = 0;
+    sc->rtol = rtol;
+    sc->maxit = maxit;
+  }
+}
+
+// Column `slot` of [rows][nslots] vectors: r = b on free rows, x = p = 0;
+// partial sums of ||b||^2 for batch_admit_scalar_kernel.
+__global__ void __launch_bounds__(kDotThreads) batch_admit_kernel(
+    const double* __restrict__ b, const uint8_t* __restrict__ row_free, double* __restrict__ r,
+    double* __restrict__ x, double* __restrict__ p, double* __restrict__ partial, int64_t rows,
+    int nslots, int slot) {
+  double v = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double bv = row_free[i] ? b[i] : 0.0;
+    const int64_t e = i * nslots + slot;
+    r[e] = bv;
+    x[e] = 0.0;
+    p[e] = 0.0;
+    v += bv * bv;
+  }
+  block_store_partials(v, 1, partial);
+}
+
+__global__ void batch_admit_scalar_kernel(PcgScalars* sc, const double* partial, int slot) {
+  const double bn = sqrt(sum_partials_warp(partial, 0));
+  if (threadIdx.x == 0) {
+    start_column(sc, slot, bn, true);
+    sc->any_active |= sc->active[slot];
   }
 }
 
 // rho_new = r.z; beta = rho_new/rho (0 on the first iteration); rho = rho_new
 __global__ void pcg_beta_kernel(PcgScalars* sc, const double* partial, int nrhs) {
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int first = sc->first;
-  __syncthreads();
   if (q < nrhs) {
     const double rn = sum_partials_warp(partial, q);
-    if (lane == 0) {
+    if (lane == 0 && sc->active[q]) {
       double beta = 0.0;
-      if (!first && sc->rho[q] != 0.0) beta = rn / sc->rho[q];
+      if (!sc->first[q] && sc->rho[q] != 0.0) beta = rn / sc->rho[q];
       if (!isfinite(rn) || !isfinite(beta)) {
-        if (sc->active[q]) sc->breakdown = 1;
+        sc->broken[q] = 1;
+        sc->breakdown = 1;
         beta = 0.0;
       }
       sc->beta[q] = beta;
       sc->rho[q] = rn;
+      sc->first[q] = 0;
     }
   }
-  if (threadIdx.x == 0) sc->first = 0;
 }
 
 template <typename TZ>
@@ -202,12 +247,14 @@ __global__ void pcg_alpha_kernel(PcgScalars* sc, const double* partial, int nrhs
   const double pq = sum_partials_warp(partial, q);
   if (lane != 0) return;
   double alpha = 0.0;
-  if (sc->active[q]) {
+  if (sc->active[q] && !sc->broken[q]) {
     if (!(pq > 0.0) || !isfinite(pq)) {
+      sc->broken[q] = 1;
       sc->breakdown = 1;
     } else {
       alpha = sc->rho[q] / pq;
       if (!isfinite(alpha)) {
+        sc->broken[q] = 1;
         sc->breakdown = 1;
         alpha = 0.0;
       }
@@ -246,10 +293,18 @@ __global__ void pcg_check_kernel(PcgScalars* sc, const double* partial, int nrhs
   if (lane == 0) {
     int a = 0, b = 0;
     if (q < nrhs && sc->active[q]) {
-      sc->rnorm[q] = rn;
-      sc->iters[q] += 1;
-      a = rn <= sc->rtol * sc->bnorm[q] ? 0 : 1;
-      b = isfinite(rn) ? 0 : 1;
+      if (sc->broken[q] || !isfinite(rn)) {
+        sc->broken[q] = 1;
+        b = 1;
+      } else {
+        sc->rnorm[q] = rn;
+        sc->iters[q] += 1;
+        a = rn <= sc->rtol * sc->bnorm[q] ? 0 : 1;
+        if (a && sc->iters[q] >= sc->maxit) {
+          sc->failed[q] = 1;
+          a = 0;
+        }
+      }
       sc->active[q] = a;
     }
     act[q] = a;
@@ -263,7 +318,7 @@ __global__ void pcg_check_kernel(PcgScalars* sc, const double* partial, int nrhs
       brk |= bad[j];
     }
     if (brk) sc->breakdown = 1;
-    sc->any_active = sc->breakdown ? 0 : any;
+    sc->any_active = any;
   }
 }
 
@@ -344,8 +399,22 @@ cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r,
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_start(PcgScalars* sc, const double* partial, int nrhs, double rtol,
-                             cudaStream_t s) {
-  pcg_start_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs, rtol);
+                             int maxit, cudaStream_t s) {
+  pcg_start_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs, rtol, maxit);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_reset(PcgScalars* sc, double rtol, int maxit, cudaStream_t s) {
+  batch_reset_kernel<<<1, 32, 0, s>>>(sc, rtol, maxit);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double* r, double* x,
+                               double* p, double* partial, PcgScalars* sc, int64_t rows,
+                               int nslots, int slot, cudaStream_t s) {
+  batch_admit_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, row_free, r, x, p, partial, rows,
+                                                       nslots, slot);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_admit_scalar_kernel<<<1, 32, 0, s>>>(sc, partial, slot);
   return cudaGetLastError();
 }
 template <typename TZ>

@@ -25,6 +25,7 @@ namespace nnmg {
 constexpr int kMaxDegree = 4;
 constexpr int kMaxN = kMaxDegree + 1;
 constexpr int kMaxRhs = 16;
+constexpr int kCoarseMaxSegments = 16;  // column segments of the coarse solve
 
 // 1D tables for one degree k (n = k+1 points), passed to kernels by value.
 //   S[q][l]  = L_l(g_q): Gauss-Lobatto Lagrange basis at Gauss point q
@@ -123,6 +124,7 @@ struct DevLevel {
   int n_free_rows = 0;
   int32_t* free_rows = nullptr;      // [n_free_rows]
   double* coarse_inv = nullptr;      // [n_free_rows][n_free_rows]
+  double* coarse_partial = nullptr;  // [kCoarseMaxSegments][n_free_rows][kMaxRhs]
 };
 
 // ---------------------------------------------------------------- kernels
@@ -138,9 +140,14 @@ cudaError_t launch_locate(const DevLevel& coarse, const double* points, const in
                           const double* aabb, const BucketGeom& g, int32_t* out_cell,
                           double* out_xi, cudaStream_t s);
 
+// units = (cell, right-hand side) pairs per block; 0 selects the default rule.
 template <typename T>
 cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, double lambda,
-                            double mu, cudaStream_t s);
+                            double mu, cudaStream_t s, int units = 0);
+// Legal units-per-block choices of the operator kernel for this level (for the
+// autotuner); returns how many were written to out.
+template <typename T>
+int operator_unit_candidates(const DevLevel& L, int nrhs, int* out, int max_out);
 template <typename T>
 cudaError_t launch_prolongate_add(const DevLevel& fine, const DevLevel& coarse, const T* xc,
                                   T* xf, int nrhs, cudaStream_t s);
@@ -163,6 +170,8 @@ template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* a, TO* b, int64_t n, cudaStream_t s);
 
 // PCG (FP64) helpers.  Per-column scalars live in a device struct.
+// Per-column state: columns are independent, so a column can be (re)started
+// between iterations while the others continue (continuous batching).
 struct PcgScalars {
   double rho[kMaxRhs];
   double alpha[kMaxRhs];
@@ -171,9 +180,12 @@ struct PcgScalars {
   double rnorm[kMaxRhs];
   int active[kMaxRhs];
   int iters[kMaxRhs];
-  int first;
+  int first[kMaxRhs];    // 1 until the column's first beta step (beta = 0)
+  int failed[kMaxRhs];   // reached maxit without convergence
+  int broken[kMaxRhs];   // p.Ap <= 0 or a non-finite scalar
   int any_active;
-  int breakdown;
+  int breakdown;         // any column broken
+  int maxit;
   double rtol;
 };
 constexpr int kDotBlocks = 152 * 4;
@@ -184,7 +196,13 @@ cudaError_t launch_dot_partial(const double* a, const TB* b, double* partial, in
 cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r, double* x,
                             double* p, double* partial, int64_t rows, int nrhs, cudaStream_t s);
 cudaError_t launch_pcg_start(PcgScalars* sc, const double* partial, int nrhs, double rtol,
-                             cudaStream_t s);
+                             int maxit, cudaStream_t s);
+// Continuous batching: reset every column to inactive; start column `slot`
+// from the right-hand side b [rows] (r = b on free rows, x = p = 0).
+cudaError_t launch_batch_reset(PcgScalars* sc, double rtol, int maxit, cudaStream_t s);
+cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double* r, double* x,
+                               double* p, double* partial, PcgScalars* sc, int64_t rows,
+                               int nslots, int slot, cudaStream_t s);
 template <typename TZ>
 cudaError_t launch_pcg_beta_p(PcgScalars* sc, const double* partial, const TZ* z, double* p,
                               int64_t rows, int nrhs, cudaStream_t s);

@@ -6,6 +6,7 @@
 // per (precision or mode, nrhs) into a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <new>
 #include <tuple>
@@ -41,6 +42,11 @@ struct nnmg_handle {
   PcgScalars* h_sc = nullptr;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (kind, prec/mode, nrhs)
   std::map<std::tuple<int, int, int>, int> runs;
+  std::map<std::tuple<int, int, int>, int> op_units;  // (level, precision, nrhs) -> units
+  // continuous batching state
+  int batch_mode = -1, batch_slots = 0;
+  cudaEvent_t batch_ev = nullptr;
+  bool batch_inflight = false;
 };
 
 namespace {
@@ -131,6 +137,60 @@ int ensure_pcg(nnmg_handle* h) {
   return NNMG_OK;
 }
 
+// ------------------------------------------------------------------ autotuner
+// Units per block of the operator kernel for (level, precision, nrhs): on first
+// use every legal choice is timed (one warm-up and three timed launches on
+// scratch vectors, CUDA events) and the fastest is kept for the handle's
+// lifetime.  Never runs during stream capture (the default rule is used then)
+// and is skipped when the environment sets NNMG_AUTOTUNE=0.
+template <typename T>
+int op_units(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
+  const int prec = sizeof(T) == 8 ? NNMG_F64 : NNMG_F32;
+  auto key = std::make_tuple(level, prec, nrhs);
+  auto it = h->op_units.find(key);
+  if (it != h->op_units.end()) return it->second;
+  static const bool enabled = [] {
+    const char* e = getenv("NNMG_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!enabled || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return 0;
+  const DevLevel& L = h->lv[level];
+  int cand[8];
+  const int nc = operator_unit_candidates<T>(L, nrhs, cand, 8);
+  int best = 0;
+  if (nc > 1 && L.n_cells > 0) {
+    T *x = nullptr, *y = nullptr;
+    const size_t n = (size_t)L.rows * nrhs;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&x, n * sizeof(T)) == cudaSuccess && cudaMalloc(&y, n * sizeof(T)) == cudaSuccess &&
+        cudaMemsetAsync(x, 0, n * sizeof(T), s) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+        cudaEventCreate(&e1) == cudaSuccess) {
+      float best_ms = 1e30f;
+      for (int c = 0; c < nc; ++c) {
+        bool ok = launch_operator<T>(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, cand[c]) == cudaSuccess;
+        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+        for (int r = 0; r < 3 && ok; ++r)
+          ok = launch_operator<T>(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, cand[c]) == cudaSuccess;
+        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.f;
+        if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best = cand[c];
+        }
+      }
+    }
+    cudaGetLastError();  // a rejected candidate must not leave a sticky launch error
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (x) cudaFree(x);
+    if (y) cudaFree(y);
+  }
+  h->op_units[key] = best;
+  return best;
+}
+
 // ------------------------------------------------------------------ V-cycle
 // Algorithm 1 with Chebyshev-Jacobi smoothing (Sec. 4): pre-smoothing from a
 // zero guess (m steps, m-1 operator applications), residual, restriction
@@ -153,17 +213,18 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
     const T* f = l == top ? f_top : W.f[l];
     T *x = W.x[l], *t = W.t[l], *d = W.d[l];
     const T* dinv = dinv_of<T>(L);
+    const int ou = op_units<T>(h, l, nrhs, s);
     const double a = L.cheb_a, b = L.cheb_b;
     const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
     RET(launch_cheb_init<T>(f, dinv, d, x, 1.0 / theta, L.rows, nrhs, s));
     double rho = 1.0 / sigma;
     for (int j = 1; j < m; ++j) {
-      RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s));
+      RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
       const double rn = 1.0 / (2.0 * sigma - rho);
       RET(launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
       rho = rn;
     }
-    RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s));
+    RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
     RET(launch_residual<T>(f, t, d, L.rows, nrhs, s));
     RET(launch_restrict<T>(L, h->lv[l - 1], d, W.f[l - 1], W.scratch[l], nrhs, s));
   }
@@ -177,13 +238,14 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
     T *x = W.x[l], *t = W.t[l], *d = W.d[l];
     const T* dinv = dinv_of<T>(L);
     RET(launch_prolongate_add<T>(L, h->lv[l - 1], W.x[l - 1], x, nrhs, s));
+    const int ou = op_units<T>(h, l, nrhs, s);
     const double a = L.cheb_a, b = L.cheb_b;
     const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
     double rho = 1.0 / sigma;
-    RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s));
+    RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
     RET(launch_cheb_step<T>(f, t, dinv, d, x, 0.0, 1.0 / theta, L.rows, nrhs, s));
     for (int j = 1; j < m; ++j) {
-      RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s));
+      RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
       const double rn = 1.0 / (2.0 * sigma - rho);
       RET(launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
       rho = rn;
@@ -215,7 +277,9 @@ cudaError_t enqueue_pcg_iter(nnmg_handle* h, int mode, int nrhs, cudaStream_t s)
     if ((e = launch_dot_partial<double>(h->pr, z, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
     if ((e = launch_pcg_beta_p<double>(h->sc, h->partial, z, h->pp, rows, nrhs, s)) != cudaSuccess) return e;
   }
-  if ((e = launch_operator<double>(L, h->pp, h->pq, nrhs, h->opt.lambda, h->opt.mu, s)) != cudaSuccess) return e;
+  if ((e = launch_operator<double>(L, h->pp, h->pq, nrhs, h->opt.lambda, h->opt.mu, s,
+                                   op_units<double>(h, top, nrhs, s))) != cudaSuccess)
+    return e;
   if ((e = launch_dot_partial<double>(h->pp, h->pq, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
   if ((e = launch_pcg_alpha(h->sc, h->partial, nrhs, s)) != cudaSuccess) return e;
   if ((e = launch_pcg_update(h->sc, h->pp, h->pq, h->px, h->pr, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
@@ -406,6 +470,7 @@ int setup_coarse(nnmg_handle* h, DevLevel& L, cudaStream_t s) {
     return NNMG_CHOLESKY_FAIL;
   }
   CK(dalloc(h, &L.coarse_inv, (size_t)n * n));
+  CK(dalloc(h, &L.coarse_partial, (size_t)kCoarseMaxSegments * n * kMaxRhs));
   CK(cudaMemcpy(L.coarse_inv, inv.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice));
   return NNMG_OK;
 }
@@ -594,6 +659,7 @@ int check_vec_args(nnmg_handle* h, int level, int precision, int nrhs) {
 }
 
 void destroy_impl(nnmg_handle* h) {
+  if (h->batch_ev) cudaEventDestroy(h->batch_ev);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -829,11 +895,13 @@ int nnmg_apply_operator(nnmg_handle* h, int level, int precision, const void* x,
   cudaStream_t s = (cudaStream_t)stream;
   const DevLevel& L = h->lv[level];
   const size_t ts = precision == NNMG_F64 ? sizeof(double) : sizeof(float);
+  const int ou = precision == NNMG_F64 ? op_units<double>(h, level, nrhs, s)
+                                        : op_units<float>(h, level, nrhs, s);
   NNMG_CUDA(cudaMemsetAsync(y, 0, (size_t)L.rows * nrhs * ts, s));
   if (precision == NNMG_F64)
-    NNMG_CUDA(launch_operator<double>(L, (const double*)x, (double*)y, nrhs, h->opt.lambda, h->opt.mu, s));
+    NNMG_CUDA(launch_operator<double>(L, (const double*)x, (double*)y, nrhs, h->opt.lambda, h->opt.mu, s, ou));
   else
-    NNMG_CUDA(launch_operator<float>(L, (const float*)x, (float*)y, nrhs, h->opt.lambda, h->opt.mu, s));
+    NNMG_CUDA(launch_operator<float>(L, (const float*)x, (float*)y, nrhs, h->opt.lambda, h->opt.mu, s, ou));
   return NNMG_OK;
 }
 
@@ -912,6 +980,106 @@ int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
   return NNMG_OK;
 }
 
+// ------------------------------------------------------- continuous batching
+int nnmg_batch_reset(nnmg_handle* h, int mode, int nslots, double rtol, int maxit, void* stream) {
+  int rc = check_vec_args(h, 0, NNMG_F64, nslots);
+  if (rc) return rc;
+  if ((mode != NNMG_FP64_MG && mode != NNMG_FP32_MG_FP64_CG) || !(rtol > 0.0) || maxit < 1) {
+    set_error("bad mode, rtol or maxit");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = ensure_pcg(h))) return rc;
+  if ((rc = (mode == NNMG_FP32_MG_FP64_CG ? ensure_work<float>(h) : ensure_work<double>(h)))) return rc;
+  if (!h->batch_ev) NNMG_CUDA(cudaEventCreateWithFlags(&h->batch_ev, cudaEventDisableTiming));
+  const size_t n = (size_t)h->lv.back().rows * nslots * sizeof(double);
+  NNMG_CUDA(cudaMemsetAsync(h->px, 0, n, s));
+  NNMG_CUDA(cudaMemsetAsync(h->pr, 0, n, s));
+  NNMG_CUDA(cudaMemsetAsync(h->pp, 0, n, s));
+  NNMG_CUDA(cudaMemsetAsync(h->pq, 0, n, s));
+  NNMG_CUDA(launch_batch_reset(h->sc, rtol, maxit, s));
+  h->batch_mode = mode;
+  h->batch_slots = nslots;
+  h->batch_inflight = false;
+  return NNMG_OK;
+}
+
+int nnmg_batch_admit(nnmg_handle* h, int slot, const double* b, int b_on_host, void* stream) {
+  if (!h || h->batch_mode < 0 || slot < 0 || slot >= h->batch_slots || !b) {
+    set_error("nnmg_batch_admit: no batch started, bad slot or null b");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevLevel& L = h->lv.back();
+  const double* src = b;
+  if (b_on_host) {
+    NNMG_CUDA(cudaMemcpyAsync(h->pb, b, (size_t)L.rows * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = h->pb;
+  }
+  NNMG_CUDA(launch_batch_admit(src, L.row_free, h->pr, h->px, h->pp, h->partial, h->sc, L.rows,
+                               h->batch_slots, slot, s));
+  return NNMG_OK;
+}
+
+int nnmg_batch_step(nnmg_handle* h, void* stream) {
+  if (!h || h->batch_mode < 0) {
+    set_error("nnmg_batch_step: no batch started");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int mode = h->batch_mode, nslots = h->batch_slots;
+  int rc = run_graph(h, {1, mode, nslots}, s, [&](cudaStream_t st) {
+    return enqueue_pcg_iter(h, mode, nslots, st);
+  });
+  if (rc) return rc;
+  NNMG_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+  NNMG_CUDA(cudaEventRecord(h->batch_ev, s));
+  h->batch_inflight = true;
+  return NNMG_OK;
+}
+
+int nnmg_batch_poll(nnmg_handle* h, int wait, int* ready, int* active, int* iters, double* relres,
+                    int* status) {
+  if (!h || h->batch_mode < 0 || !ready) {
+    set_error("nnmg_batch_poll: no batch started");
+    return NNMG_INVALID_ARG;
+  }
+  *ready = 0;
+  if (h->batch_inflight) {
+    cudaError_t e = wait ? cudaEventSynchronize(h->batch_ev) : cudaEventQuery(h->batch_ev);
+    if (e == cudaErrorNotReady) return NNMG_OK;
+    NNMG_CUDA(e);
+    h->batch_inflight = false;
+  } else {
+    return NNMG_OK;
+  }
+  *ready = 1;
+  const PcgScalars& sc = *h->h_sc;
+  for (int q = 0; q < h->batch_slots; ++q) {
+    if (active) active[q] = sc.active[q];
+    if (iters) iters[q] = sc.iters[q];
+    if (relres) relres[q] = sc.bnorm[q] > 0 ? sc.rnorm[q] / sc.bnorm[q] : 0.0;
+    if (status)
+      status[q] = sc.broken[q] ? NNMG_BREAKDOWN : (sc.failed[q] ? NNMG_NOT_CONVERGED : NNMG_OK);
+  }
+  return NNMG_OK;
+}
+
+int nnmg_batch_retire(nnmg_handle* h, int slot, double* x, int x_on_host, void* stream) {
+  if (!h || h->batch_mode < 0 || slot < 0 || slot >= h->batch_slots || !x) {
+    set_error("nnmg_batch_retire: no batch started, bad slot or null x");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevLevel& L = h->lv.back();
+  NNMG_CUDA(cudaMemcpy2DAsync(x, sizeof(double), h->px + slot, (size_t)h->batch_slots * sizeof(double),
+                              sizeof(double), (size_t)L.rows,
+                              x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  NNMG_CUDA(cudaMemsetAsync(&h->sc->active[slot], 0, sizeof(int), s));
+  if (x_on_host) NNMG_CUDA(cudaStreamSynchronize(s));
+  return NNMG_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -923,7 +1091,7 @@ int pcg_run(nnmg_handle* h, int mode, const double* b, int nrhs, double rtol, in
   if ((rc = (mode == NNMG_FP32_MG_FP64_CG ? ensure_work<float>(h) : ensure_work<double>(h)))) return rc;
   const DevLevel& L = h->lv.back();
   NNMG_CUDA(launch_pcg_init(b, L.row_free, h->pr, h->px, h->pp, h->partial, L.rows, nrhs, s));
-  NNMG_CUDA(launch_pcg_start(h->sc, h->partial, nrhs, rtol, s));
+  NNMG_CUDA(launch_pcg_start(h->sc, h->partial, nrhs, rtol, maxit, s));
   NNMG_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   NNMG_CUDA(cudaStreamSynchronize(s));
   bool active = h->h_sc->any_active != 0;

@@ -1,0 +1,241 @@
+"""Continuous-batching solve server on one GPU.
+
+Every mesh family gets a FamilyEngine: its hierarchy (built once and cached on
+the device), a CUDA stream and a PCG over 16 independent right-hand-side
+slots (nnmg_batch_* in include/nnmg.h).  Between two PCG iterations an engine
+retires the columns that converged, returns finished requests and admits
+queued requests into the freed slots, so requests that arrive while others are
+being solved join the running solve (iteration-level batching).  Engines of
+different families step concurrently on their own streams.  A family is built
+only if its device bytes fit the memory budget; idle families are evicted
+(least recently used) to make room.
+
+The scheduler is host code; every arithmetic step runs in libnnmg's kernels.
+"""
+from __future__ import annotations
+
+import collections
+import ctypes as C
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _abi
+from . import nnmg as _nnmg
+
+
+@dataclass
+class Request:
+    rid: int
+    family: str
+    b: np.ndarray                  # host [rows, nrhs] float64
+    arrival: float = 0.0           # seconds after the start of the run
+    x: np.ndarray | None = None
+    iters: list = field(default_factory=list)
+    relres: list = field(default_factory=list)
+    status: list = field(default_factory=list)
+    t_admit: float | None = None
+    t_done: float | None = None
+    cols_left: int = 0
+
+    @property
+    def nrhs(self):
+        return self.b.shape[1]
+
+
+@dataclass
+class FamilySpec:
+    levels: list
+    degree: int
+    cheb: int = 3
+    n_components: int = 1
+    lame: tuple = (1.0, 1.0)
+
+
+class FamilyEngine:
+    def __init__(self, name, spec, nslots=16, mode=_abi.FP32_MG_FP64_CG, rtol=1e-8, maxit=200):
+        import torch
+        self.name = name
+        self.spec = spec
+        self.H = _nnmg.Hierarchy(spec.levels, spec.degree, spec.n_components, spec.lame,
+                                 spec.cheb, max_nrhs=nslots)
+        self.top = self.H.n_levels - 1
+        self.rows = self.H.rows(self.top)
+        self.free_dofs = self.H.info(self.top)[1] * spec.n_components
+        self.nslots = nslots
+        self.stream = torch.cuda.Stream()
+        self.sptr = C.c_void_p(self.stream.cuda_stream)
+        self.lib = _abi.load()
+        self.owner = [None] * nslots          # slot -> (request, column)
+        self.queue = collections.deque()
+        self.inflight = False
+        self.last_used = time.perf_counter()
+        self._chk(self.lib.nnmg_batch_reset(self.H.h, mode, nslots, rtol, maxit, self.sptr), "reset")
+        self._active = np.zeros(nslots, dtype=np.int32)
+        self._iters = np.zeros(nslots, dtype=np.int32)
+        self._rel = np.zeros(nslots)
+        self._status = np.zeros(nslots, dtype=np.int32)
+
+    def bytes(self):
+        return self.H.hierarchy_bytes() + self.H.solve_bytes(self.nslots)
+
+    def _chk(self, st, what):
+        if st != 0:
+            raise _nnmg.NNMGError(st, f"{self.name}: {what}")
+
+    def free_slots(self):
+        return sum(o is None for o in self.owner)
+
+    def busy(self):
+        return self.inflight or any(o is not None for o in self.owner) or bool(self.queue)
+
+    def admit(self, now):
+        """Move queued requests into free slots while whole requests fit."""
+        while self.queue and self.queue[0].nrhs <= self.free_slots():
+            req = self.queue.popleft()
+            req.t_admit = now
+            req.x = np.zeros((self.rows, req.nrhs))
+            req.iters = [0] * req.nrhs
+            req.relres = [0.0] * req.nrhs
+            req.status = [0] * req.nrhs
+            req.cols_left = req.nrhs
+            for j in range(req.nrhs):
+                slot = self.owner.index(None)
+                self.owner[slot] = (req, j)
+                col = np.ascontiguousarray(req.b[:, j])
+                self._chk(self.lib.nnmg_batch_admit(self.H.h, slot, col.ctypes.data, 1, self.sptr),
+                          "admit")
+
+    def step(self):
+        if any(o is not None for o in self.owner) and not self.inflight:
+            self._chk(self.lib.nnmg_batch_step(self.H.h, self.sptr), "step")
+            self.inflight = True
+            self.last_used = time.perf_counter()
+
+    def poll(self, wait=False):
+        """If the last step finished: retire finished columns; returns finished requests."""
+        if not self.inflight:
+            return None
+        ready = C.c_int(0)
+        self._chk(self.lib.nnmg_batch_poll(self.H.h, int(wait), C.byref(ready),
+                                           self._active.ctypes.data, self._iters.ctypes.data,
+                                           self._rel.ctypes.data, self._status.ctypes.data),
+                  "poll")
+        if not ready.value:
+            return None
+        self.inflight = False
+        done = []
+        for slot, o in enumerate(self.owner):
+            if o is None or self._active[slot]:
+                continue
+            req, j = o
+            col = np.empty(self.rows)
+            self._chk(self.lib.nnmg_batch_retire(self.H.h, slot, col.ctypes.data, 1, self.sptr),
+                      "retire")
+            req.x[:, j] = col
+            req.iters[j] = int(self._iters[slot])
+            req.relres[j] = float(self._rel[slot])
+            req.status[j] = int(self._status[slot])
+            self.owner[slot] = None
+            req.cols_left -= 1
+            if req.cols_left == 0:
+                done.append(req)
+        return done
+
+    def close(self):
+        self.H.close()
+
+
+class Server:
+    """Admits requests by device-memory budget and runs all families' engines."""
+
+    def __init__(self, families: dict, budget_bytes: int, nslots=16, mode=_abi.FP32_MG_FP64_CG,
+                 rtol=1e-8, maxit=200):
+        self.families = families
+        self.budget = budget_bytes
+        self.kw = dict(nslots=nslots, mode=mode, rtol=rtol, maxit=maxit)
+        self.engines: dict[str, FamilyEngine] = {}
+        self.evictions = 0
+
+    def used_bytes(self):
+        return sum(e.bytes() for e in self.engines.values())
+
+    def engine(self, name):
+        """The family's engine, building it if the budget allows (evicting idle ones)."""
+        if name in self.engines:
+            return self.engines[name]
+        eng = None
+        while True:
+            idle = [e for e in self.engines.values() if not e.busy()]
+            if eng is None:
+                eng = FamilyEngine(name, self.families[name], **self.kw)
+            if self.used_bytes() + eng.bytes() <= self.budget:
+                self.engines[name] = eng
+                return eng
+            if not idle:
+                need = eng.bytes()
+                eng.close()
+                if not self.engines:
+                    raise MemoryError(f"family {name} needs {need} bytes, budget {self.budget}")
+                return None       # wait until an engine becomes idle
+            victim = min(idle, key=lambda e: e.last_used)
+            victim.close()
+            del self.engines[victim.name]
+            self.evictions += 1
+
+    def prepare(self, names):
+        for n in names:
+            self.engine(n)
+
+    def run(self, requests, time_scale=1.0):
+        """Serve requests (sorted by arrival, seconds); returns finished requests."""
+        import torch
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = collections.deque()          # arrived, family not admitted yet
+        finished = []
+        t0 = time.perf_counter()
+        total = len(pending)
+        while len(finished) < total:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival * time_scale <= now:
+                waiting.append(pending.popleft())
+            still = collections.deque()
+            for req in waiting:
+                eng = self.engine(req.family)
+                if eng is None:
+                    still.append(req)
+                else:
+                    eng.queue.append(req)
+            waiting = still
+            progressed = False
+            for eng in list(self.engines.values()):
+                done = eng.poll(wait=False)
+                if done is not None:
+                    progressed = True
+                    t = time.perf_counter() - t0
+                    for r in done:
+                        r.t_done = t
+                        finished.append(r)
+                if not eng.inflight:
+                    eng.admit(time.perf_counter() - t0)
+                    eng.step()
+            if not progressed:
+                inflight = [e for e in self.engines.values() if e.inflight]
+                if inflight and not pending and not waiting:
+                    inflight[0].stream.synchronize()
+                else:
+                    time.sleep(0.0002)
+        torch.cuda.synchronize()
+        return finished
+
+    def close(self):
+        for e in self.engines.values():
+            e.close()
+        self.engines.clear()
+
+
+def latency_stats(finished):
+    lat = np.array([r.t_done - r.arrival for r in finished])
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean())}

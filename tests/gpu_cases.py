@@ -12,6 +12,9 @@ from tests.oracle_meshes import box_level, scramble
 CASES = {
     "c1_q1": (lambda: config_levels("c1_2d_q1"), 1, 1, (1.0, 1.0), 3, 1),
     "c1_q3": (lambda: config_levels("c1_2d_q1", n_levels=2), 3, 1, (1.0, 1.0), 3, 3),
+    "c1_q2_16rhs": (lambda: config_levels("c1_2d_q1"), 2, 1, (1.0, 1.0), 3, 16),
+    "c1_q4_5rhs": (lambda: config_levels("c1_2d_q1", n_levels=2), 4, 1, (1.0, 1.0), 3, 5),
+    "c2_q1_3lev": (lambda: config_levels("c2_3d_q2", n_levels=3), 1, 1, (1.0, 1.0), 3, 2),
     "c2_q2_3lev": (lambda: config_levels("c2_3d_q2", n_levels=3), 2, 1, (1.0, 1.0), 3, 8),
     "c3_q4_2lev": (lambda: config_levels("c3_3d_q4_deformed", n_levels=2), 4, 1, (1.0, 1.0), 5, 4),
     "c4_elast": (lambda: config_levels("c4_3d_q2_elasticity"), 2, 3, (10.0, 1.0), 4, 1),
