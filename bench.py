@@ -181,6 +181,80 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_configs(args, rank):
+    """Every configuration: setup time, then p50/p99 of timed solves (after
+    warm-up) in both modes, one JSON line per configuration."""
+    import numpy as np
+    import torch
+    from paper_2412_10910_gb300 import _abi, nnmg
+    from synthetic import config_levels, normal_rhs
+    from synthetic.meshes import CONFIGS
+
+    cases = [("c1_2d_q1", None, None), ("c2_3d_q2", None, None),
+             ("c3_3d_q4_deformed", None, None),
+             ("c3_3d_q4_deformed", "pmg", None),        # polynomial-multigrid coarse solver
+             ("c4_3d_q2_elasticity", None, None),
+             ("c4_3d_q2_elasticity", None, [(8, 2, 2), (19, 5, 5), (41, 11, 11), (85, 23, 23)])]
+    for name, variant, cells in cases:
+        cfg = CONFIGS[name]
+        levels = config_levels(name, cells=cells)
+        degs = None
+        if variant == "pmg":
+            k = cfg["degree"]
+            levels = [levels[0]] * (k - 1) + levels
+            degs = list(range(1, k)) + [k] * (len(levels) - k + 1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        H = nnmg.Hierarchy(levels, cfg["degree"], cfg["ncomp"], cfg.get("lame", (1.0, 1.0)),
+                           cfg["cheb"], max_nrhs=16, level_degrees=degs)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t
+        top = H.n_levels - 1
+        rows = H.rows(top)
+        nn, nfree, nc = H.info(top)
+        nrhs = cfg["nrhs"]
+        b = H.vector(top, nrhs)
+        if name.startswith("c1"):
+            xq = H.quadrature_points(top)
+            fq = 2 * np.pi ** 2 * np.sin(np.pi * xq[..., 0]) * np.sin(np.pi * xq[..., 1])
+            H.load_vector(top, fq.reshape(-1), b, col=0, per_qp=True)
+        elif name.startswith("c4"):
+            H.load_vector(top, np.array([0.0, 0.0, -1.0]), b, col=0)
+        else:
+            H.load_vector(top, np.ones(1), b, col=0)
+        if nrhs > 1:
+            r = normal_rhs(rows, [1000 + j for j in range(1, nrhs)])
+            b[:, 1:] = torch.tensor(r, device="cuda")
+        out = {"config": name + ("_" + variant if variant else ""),
+               "levels": [list(lv.n) for lv in levels], "level_degrees": degs, "fine_free_dofs":
+               int(nfree) * cfg["ncomp"], "nrhs": nrhs, "setup_s": setup_s,
+               "setup_dofs_per_s": int(nn) * cfg["ncomp"] / setup_s,
+               "hierarchy_bytes": H.hierarchy_bytes()}
+        for mode, tag in [(_abi.FP32_MG_FP64_CG, "fp32_mg_fp64_cg"), (_abi.FP64_MG, "fp64_mg"),
+                          (_abi.FP32_MG_DW_CG, "fp32_mg_dw_cg")]:
+            x = torch.zeros_like(b)
+            steps = args.steps if nfree * nrhs < 5e6 else max(5, args.steps // 10)
+            for _ in range(max(3, args.warmup)):
+                st, its, rel = H.pcg(b, x, mode=mode)
+            ts = []
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st, its, rel = H.pcg(b, x, mode=mode)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ts.sort()
+            med = ts[len(ts) // 2]
+            out[tag] = {"p50_ms": med, "p99_ms": ts[min(len(ts) - 1, int(0.99 * len(ts)))],
+                        "solves": steps, "iterations": [int(i) for i in its],
+                        "max_relres": float(max(rel)),
+                        "solved_dofs_per_s": nfree * cfg["ncomp"] * nrhs / (med / 1e3)}
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        H.close()
+
+
 def run_serving(args, rank):
     """Serving mix: 12 cached mesh families, Poisson arrivals, continuous batching."""
     import torch
@@ -236,7 +310,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["solve", "solve64", "vcycle", "op64", "op32", "serving"],
+    ap.add_argument("--only", choices=["solve", "solve64", "vcycle", "op64", "op32", "serving",
+                                       "configs"],
                     default=None, help="run only one timed section (for profiler launch lists), "
                     "or the serving mix")
     ap.add_argument("--requests", type=int, default=2000, help="serving mix: number of requests")
@@ -258,6 +333,8 @@ def main():
     torch.cuda.set_device(local)
     if args.only == "serving":
         return run_serving(args, rank)
+    if args.only == "configs":
+        return run_configs(args, rank)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
@@ -361,6 +438,9 @@ def main():
     # ---- comparator: plain FP64 multigrid
     ts64, (st64, its64, rel64) = timed(lambda: solve(_abi.FP64_MG), max(2, args.steps // 3), 1)
     ms64 = max_over_ranks(statistics.mean(ts64))
+    # ---- variant: the CG's operator in double-word arithmetic on the FP32 pipes
+    tsdw, (stdw, itsdw, reldw) = timed(lambda: solve(_abi.FP32_MG_DW_CG), max(3, args.steps // 2), 2)
+    msdw = max_over_ranks(statistics.mean(tsdw))
 
     # ---- V-cycle and operator throughput (fine level, all RHS)
     r32 = torch.randn(rows, nrhs, dtype=torch.float32, device="cuda")
@@ -372,6 +452,7 @@ def main():
     x32 = x64.float()
     y32 = torch.empty_like(x32)
     top32, _ = timed(lambda: H.apply(top, x32, y32), 10, 3)
+    topdw, _ = timed(lambda: H.apply(top, x64, y64, double_word=True), 10, 3)
 
     # ---- end to end through the host-buffer C call
     bh = torch.empty(rows * nrhs, dtype=torch.float64, pin_memory=True)
@@ -406,9 +487,15 @@ def main():
         "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
         "fp64_mg": {"value": dofs * world / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                     "iterations": [int(i) for i in its64]},
+        "fp32_mg_dw_cg": {"value": dofs * world / (msdw / 1e3), "unit": UNIT, "ms_per_step": msdw,
+                          "iterations": [int(i) for i in itsdw],
+                          "max_relres": float(max(reldw)),
+                          "note": "CG operator in double-word (2 x FP32, ~48-bit) arithmetic; "
+                                  "vectors, dots and updates FP64"},
         "vcycle_gdofs": dofs / (statistics.mean(tv) / 1e3) / 1e9,
         "operator_gdofs": {"f32": n_nodes * nrhs / (statistics.mean(top32) / 1e3) / 1e9,
-                           "f64": n_nodes * nrhs / (op64_ms / 1e3) / 1e9},
+                           "f64": n_nodes * nrhs / (op64_ms / 1e3) / 1e9,
+                           "f64_double_word": n_nodes * nrhs / (statistics.mean(topdw) / 1e3) / 1e9},
         "roofline": {"kernel": "op3d_kernel<2,double,1> (FP64 fine-level operator, 8 RHS)",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,

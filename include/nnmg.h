@@ -64,18 +64,28 @@ enum nnmg_status {
   NNMG_BREAKDOWN = 8        /* PCG met p.Ap <= 0 or a non-finite scalar           */
 };
 
-enum nnmg_precision { NNMG_F32 = 0, NNMG_F64 = 1 };
+/* NNMG_F64_DW (nnmg_apply_operator only): FP64 vectors, arithmetic in
+ * double-word form (pairs of floats, about 48 significand bits) on the FP32
+ * pipes, which GB300 runs 61x faster than its FP64 pipe. */
+enum nnmg_precision { NNMG_F32 = 0, NNMG_F64 = 1, NNMG_F64_DW = 2 };
 
 enum nnmg_mode {
   NNMG_FP64_MG = 0,          /* V-cycle and CG in double precision                */
-  NNMG_FP32_MG_FP64_CG = 1   /* V-cycle in single precision inside a double CG (Sec. 4) */
+  NNMG_FP32_MG_FP64_CG = 1,  /* V-cycle in single precision inside a double CG (Sec. 4) */
+  NNMG_FP32_MG_DW_CG = 2     /* as 1, with the CG's operator A p in double-word
+                                arithmetic (vectors, dots and updates stay FP64) */
 };
 
 /* One level of the hierarchy: a conforming quad (dim 2) or hex (dim 3) mesh.
  * vertices: host, [n_vertices][dim] doubles.
  * cells: host, [n_cells][2^dim] vertex indices; local corner v = b0 + 2 b1 + 4 b2
  *   where b_d is the corner's offset bit in reference direction d.
- * dirichlet_vertex: host, [n_vertices] flags (NULL = no Dirichlet boundary). */
+ * dirichlet_vertex: host, [n_vertices] flags (NULL = no Dirichlet boundary).
+ * degree: polynomial degree of this level, 1..4, or 0 for options.degree.
+ *   Repeating the coarsest mesh with degrees 1, 2, .., k below the Q_k levels
+ *   gives the polynomial-multigrid coarse solver of Sec. 2 ("Coarse grid
+ *   solvers", Fig. hp_MG): the transfers between degrees on one mesh are the
+ *   same point evaluations (nested there), and the direct solve acts on Q1. */
 typedef struct {
   int dim;
   int64_t n_vertices;
@@ -83,6 +93,7 @@ typedef struct {
   int64_t n_cells;
   const int32_t* cells;
   const uint8_t* dirichlet_vertex;
+  int degree;
 } nnmg_level_desc;
 
 /* Solver options (Sec. 4 solver settings; values in brackets are defaults).

@@ -47,17 +47,22 @@ class OracleLevel:
 
 class OracleHierarchy:
     def __init__(self, levels, degree, ncomp=1, lame=(1.0, 1.0), cheb_degree=3,
-                 lanczos_steps=12, smoothing_range=20.0, safety=1.2, build_solver=True):
+                 lanczos_steps=12, smoothing_range=20.0, safety=1.2, build_solver=True,
+                 level_degrees=None):
+        """level_degrees: optional per-level degrees (0 = degree), coarse -> fine; repeating
+        the coarsest mesh with degrees 1..k gives polynomial coarsening on that mesh
+        (Sec. 2, "Coarse grid solvers")."""
         self.degree = degree
         self.ncomp = ncomp
-        self.levels = [OracleLevel(lv, degree, ncomp, lame) for lv in levels]
+        degs = [d or degree for d in (level_degrees or [0] * len(levels))]
+        self.levels = [OracleLevel(lv, k, ncomp, lame) for lv, k in zip(levels, degs)]
         self.A = [lv.assemble() for lv in self.levels]
         self.P = [None]
         self.loc = [None]
         for l in range(1, len(self.levels)):
             f, c = self.levels[l], self.levels[l - 1]
             cd = dict(vertices=c.vertices, cells=c.cells, node_of=c.node_of, free=~c.constrained)
-            Pn, cell, xi = transfer.transfer_matrix(f.points, f.free_nodes, cd, degree, f.dim)
+            Pn, cell, xi = transfer.transfer_matrix(f.points, f.free_nodes, cd, c.k, f.dim)
             Pd = sp.kron(Pn, sp.identity(ncomp), format="csr") if ncomp > 1 else Pn
             self.P.append(Pd.tocsr())
             self.loc.append((cell, xi))

@@ -14,8 +14,8 @@ distorted cell the iterates of a point outside it can wander into [0,1]^d
 without converging, and such an iterate is not a preimage).  A cell accepts
 the point when Newton converged and xi lies in [-1e-10, 1 + 1e-10]^d; the
 first accepting cell wins.  If no cell accepts, the converged cell whose xi is
-nearest to [0,1]^d is taken and xi is projected onto [0,1]^d (Eq.
-closest_point).
+nearest to [0,1]^d is taken (lowest index on ties) and xi is projected onto
+[0,1]^d (Eq. closest_point).
 Restriction is R = P^T (Eq. residual2).
 """
 import numpy as np

@@ -7,13 +7,14 @@ LIB_PATH = os.path.join(HERE, "libnnmg.so")
 
 OK, INVALID_ARG, BAD_MESH, POINT_NOT_FOUND, CHOLESKY_FAIL, OUT_OF_MEMORY, CUDA_ERROR, \
     NOT_CONVERGED, BREAKDOWN = range(9)
-F32, F64 = 0, 1
-FP64_MG, FP32_MG_FP64_CG = 0, 1
+F32, F64, F64_DW = 0, 1, 2
+FP64_MG, FP32_MG_FP64_CG, FP32_MG_DW_CG = 0, 1, 2
 
 
 class LevelDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_vertices", C.c_int64), ("vertices", C.c_void_p),
-                ("n_cells", C.c_int64), ("cells", C.c_void_p), ("dirichlet_vertex", C.c_void_p)]
+                ("n_cells", C.c_int64), ("cells", C.c_void_p), ("dirichlet_vertex", C.c_void_p),
+                ("degree", C.c_int)]
 
 
 class Options(C.Structure):

@@ -17,10 +17,28 @@
 // entry (scatter is atomic).
 #include <algorithm>
 
+#include "dword.h"
 #include "nnmg_internal.h"
 
 namespace nnmg {
 namespace {
+
+// Arithmetic type T and the type of vectors in memory: float and double work
+// in place; the double-word type dw reads and writes FP64 vectors.
+template <typename T>
+struct io_of {
+  using type = T;
+};
+template <>
+struct io_of<dw> {
+  using type = double;
+};
+__device__ __forceinline__ float to_arith(float v, float) { return v; }
+__device__ __forceinline__ double to_arith(double v, double) { return v; }
+__device__ __forceinline__ dw to_arith(double v, dw) { return dw_from_double(v); }
+__device__ __forceinline__ void add_out(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void add_out(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void add_out(double* p, dw v) { atomicAdd(p, dw_to_double(v)); }
 
 template <int N, typename T>
 __device__ __forceinline__ void apply(const T (&M)[kMaxN][kMaxN], const T* in, T* out) {
@@ -69,7 +87,8 @@ __device__ __forceinline__ void elastic_flux(const T (&g)[3][3], const T (&K)[3]
 
 template <int K, typename T, int NC>
 __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __restrict__ metric,
-                            const T* __restrict__ x, T* __restrict__ y, int64_t n_cells, int nrhs,
+                            const typename io_of<T>::type* __restrict__ x,
+                            typename io_of<T>::type* __restrict__ y, int64_t n_cells, int nrhs,
                             int U, Basis1D<T> B, T lambda, T mu) {
   constexpr int N = K + 1, N2 = N * N, NQ = N2 * N;
   constexpr int NM = NC == 1 ? 6 : 9;
@@ -103,7 +122,8 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
   for (int c = 0; c < NC; ++c) {
     T u[N], v[N];
 #pragma unroll
-    for (int l = 0; l < N; ++l) u[l] = dof[l] >= 0 ? x[(int64_t)dof[l] * rs + c * nrhs + rhs] : T(0);
+    for (int l = 0; l < N; ++l)
+      u[l] = dof[l] >= 0 ? to_arith(x[(int64_t)dof[l] * rs + c * nrhs + rhs], T()) : T(0);
     apply<N>(B.S, u, v);
 #pragma unroll
     for (int q = 0; q < N; ++q) S(3 * c, a + N * b + N2 * q) = v[q];
@@ -241,14 +261,15 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     apply_t<N>(B.S, f, o);
 #pragma unroll
     for (int l = 0; l < N; ++l)
-      if (dof[l] >= 0) atomicAdd(&y[(int64_t)dof[l] * rs + c * nrhs + rhs], o[l]);
+      if (dof[l] >= 0) add_out(&y[(int64_t)dof[l] * rs + c * nrhs + rhs], o[l]);
   }
 }
 
 // 2D Poisson: one thread per x-column (i = a) or y-row.
 template <int K, typename T>
 __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __restrict__ metric,
-                            const T* __restrict__ x, T* __restrict__ y, int64_t n_cells, int nrhs,
+                            const typename io_of<T>::type* __restrict__ x,
+                            typename io_of<T>::type* __restrict__ y, int64_t n_cells, int nrhs,
                             int U, Basis1D<T> B) {
   constexpr int N = K + 1, NQ = N * N;
   extern __shared__ unsigned char smem_raw[];
@@ -265,7 +286,7 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       dof[j] = act ? cell_nodes[cell * NQ + a + N * j] : -1;
-      u[j] = dof[j] >= 0 ? x[(int64_t)dof[j] * nrhs + rhs] : T(0);
+      u[j] = dof[j] >= 0 ? to_arith(x[(int64_t)dof[j] * nrhs + rhs], T()) : T(0);
     }
     apply<N>(B.S, u, v);
 #pragma unroll
@@ -324,7 +345,7 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     apply_t<N>(B.S, f, o);
 #pragma unroll
     for (int j = 0; j < N; ++j)
-      if (dof[j] >= 0) atomicAdd(&y[(int64_t)dof[j] * nrhs + rhs], o[j]);
+      if (dof[j] >= 0) add_out(&y[(int64_t)dof[j] * nrhs + rhs], o[j]);
   }
 }
 
@@ -454,6 +475,32 @@ void pick_basis<float>(int k, Basis1D<float>* b) {
   Basis1D<double> d;
   make_basis(k, &d, b);
 }
+template <>
+void pick_basis<dw>(int k, Basis1D<dw>* b) {
+  Basis1D<double> d;
+  Basis1D<float> f;
+  make_basis(k, &d, &f);
+  for (int i = 0; i < kMaxN; ++i) {
+    for (int j = 0; j < kMaxN; ++j) {
+      b->S[i][j] = dw_split_host(d.S[i][j]);
+      b->Dg[i][j] = dw_split_host(d.Dg[i][j]);
+      b->DS[i][j] = dw_split_host(d.DS[i][j]);
+    }
+    b->gl[i] = dw_split_host(d.gl[i]);
+    b->gl_scale[i] = dw_split_host(d.gl_scale[i]);
+    b->gx[i] = dw_split_host(d.gx[i]);
+    b->gw[i] = dw_split_host(d.gw[i]);
+  }
+}
+
+template <typename T>
+T arith_from_double(double v) {
+  return (T)v;
+}
+template <>
+dw arith_from_double<dw>(double v) {
+  return dw_split_host(v);
+}
 
 struct OpConfig {
   int U;
@@ -508,8 +555,9 @@ inline int unit_candidates(int lines, int nrhs, int max_threads, size_t per_unit
 }
 
 template <int K, typename T, int NC>
-cudaError_t run3d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs, double lambda,
-                  double mu, cudaStream_t s, int units) {
+cudaError_t run3d(const DevLevel& L, const T* metric, const typename io_of<T>::type* x,
+                  typename io_of<T>::type* y, int nrhs, double lambda, double mu, cudaStream_t s,
+                  int units) {
   constexpr int N = K + 1;
   Basis1D<T> B;
   pick_basis<T>(K, &B);
@@ -523,13 +571,13 @@ cudaError_t run3d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs
     smem_set = c.smem;
   }
   kern<<<c.blocks, c.threads, c.smem, s>>>(L.cell_nodes, metric, x, y, L.n_cells, nrhs, c.U, B,
-                                           (T)lambda, (T)mu);
+                                           arith_from_double<T>(lambda), arith_from_double<T>(mu));
   return cudaGetLastError();
 }
 
 template <int K, typename T>
-cudaError_t run2d(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs, cudaStream_t s,
-                  int units) {
+cudaError_t run2d(const DevLevel& L, const T* metric, const typename io_of<T>::type* x,
+                  typename io_of<T>::type* y, int nrhs, cudaStream_t s, int units) {
   constexpr int N = K + 1;
   Basis1D<T> B;
   pick_basis<T>(K, &B);
@@ -546,6 +594,8 @@ template <>
 const double* metric_of<double>(const DevLevel& L) { return L.metric64; }
 template <>
 const float* metric_of<float>(const DevLevel& L) { return L.metric32; }
+template <>
+const dw* metric_of<dw>(const DevLevel& L) { return reinterpret_cast<const dw*>(L.metric_dw); }
 
 }  // namespace
 
@@ -569,10 +619,12 @@ bool reg_eligible(const DevLevel& L) {
 }
 
 template <typename T>
-cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, double lambda,
-                            double mu, cudaStream_t s, int units) {
+cudaError_t launch_operator_impl(const DevLevel& L, const typename io_of<T>::type* x,
+                                 typename io_of<T>::type* y, int nrhs, double lambda, double mu,
+                                 cudaStream_t s, int units) {
   if (L.n_cells == 0) return cudaSuccess;
   const T* m = metric_of<T>(L);
+  if (!m) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
     if (reg_eligible<T>(L) && units <= 0) {
 #define NNMG_REG(D, K) if (L.dim == D && L.k == K) return run_reg<D, K, T>(L, m, x, y, nrhs, s);
@@ -606,6 +658,17 @@ cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, doubl
 }
 
 template <typename T>
+cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, double lambda,
+                            double mu, cudaStream_t s, int units) {
+  return launch_operator_impl<T>(L, x, y, nrhs, lambda, mu, s, units);
+}
+
+cudaError_t launch_operator_dw(const DevLevel& L, const double* x, double* y, int nrhs,
+                               double lambda, double mu, cudaStream_t s, int units) {
+  return launch_operator_impl<dw>(L, x, y, nrhs, lambda, mu, s, units);
+}
+
+template <typename T>
 int operator_unit_candidates(const DevLevel& L, int nrhs, int* out, int max_out) {
   int lines = 0, mt = 256;
   size_t per_unit = 0;
@@ -631,5 +694,6 @@ template cudaError_t launch_operator<double>(const DevLevel&, const double*, dou
                                              double, cudaStream_t, int);
 template int operator_unit_candidates<float>(const DevLevel&, int, int*, int);
 template int operator_unit_candidates<double>(const DevLevel&, int, int*, int);
+template int operator_unit_candidates<dw>(const DevLevel&, int, int*, int);
 
 }  // namespace nnmg

@@ -329,24 +329,39 @@ __global__ void locate_kernel(const double* __restrict__ vertices, const int32_t
     if (ok) found = c;
   }
   if (found < 0) {
-    // nearest point over all cells (Sec. 3.3 Eq. closest_point)
+    // Nearest point (Sec. 3.3 Eq. closest_point): the converged cell whose xi
+    // is nearest to [0,1]^d, first searched among the cells listed in the 3^d
+    // buckets around the point (a point outside a curved boundary lies within
+    // about one coarse cell of its owner), then, if none converged, over all
+    // cells.  Ties keep the lowest cell index.
     double best = INFINITY;
     double bxi[3] = {0, 0, 0};
-    for (int64_t c = 0; c < nc; ++c) {
+    auto consider = [&](int c) {
       load_corners<D>(vertices, cells, c, X);
-      if (!newton<D>(X, p, xi)) continue;
+      if (!newton<D>(X, p, xi)) return;
       double dd = 0.0;
       for (int d = 0; d < D; ++d) {
         const double e = xi[d] - fmin(fmax(xi[d], 0.0), 1.0);
         dd += e * e;
       }
       dd = sqrt(dd);
-      if (dd < best) {
+      if (dd < best || (dd == best && c < found)) {
         best = dd;
-        found = (int)c;
+        found = c;
         for (int d = 0; d < D; ++d) bxi[d] = xi[d];
       }
-    }
+    };
+    const int lo0 = max(bi[0] - 1, 0), hi0 = min(bi[0] + 1, g.nb[0] - 1);
+    const int lo1 = D > 1 ? max(bi[1] - 1, 0) : 0, hi1 = D > 1 ? min(bi[1] + 1, g.nb[1] - 1) : 0;
+    const int lo2 = D > 2 ? max(bi[2] - 1, 0) : 0, hi2 = D > 2 ? min(bi[2] + 1, g.nb[2] - 1) : 0;
+    for (int z = lo2; z <= hi2; ++z)
+      for (int y = lo1; y <= hi1; ++y)
+        for (int x = lo0; x <= hi0; ++x) {
+          const int64_t nbk = x + (int64_t)g.nb[0] * (y + (int64_t)g.nb[1] * z);
+          for (int j = bstart[nbk]; j < bstart[nbk + 1]; ++j) consider(bcells[j]);
+        }
+    if (found < 0)
+      for (int64_t c = 0; c < nc; ++c) consider((int)c);
     for (int d = 0; d < D; ++d) xi[d] = bxi[d];
   }
   out_cell[i] = found;

@@ -1,5 +1,9 @@
 // Non-nested transfer kernels and the coarsest-level solve.
 //
+// The kernels are instantiated on the coarse level's degree (the basis they
+// evaluate); the fine level may have another degree (polynomial coarsening on
+// one mesh, Sec. 2 "Coarse grid solvers").
+//
 // Prolongation x_f += P x_c (Sec. 2, P[i,j] = phi^{l-1}_j(x_i); Sec. 3.2,
 // Eqs. local_evaluation, tensor_product_evaluation): one block per coarse cell
 // stages the cell's (k+1)^d coarse values for all channels in shared memory;
@@ -279,7 +283,7 @@ cudaError_t launch_prolongate_add(const DevLevel& fine, const DevLevel& coarse, 
   if (coarse.n_cells == 0) return cudaSuccess;
   const int nch = fine.ncomp * nrhs;
 #define NNMG_P(D, K) \
-  if (fine.dim == D && fine.k == K) return prolong_dk<D, K, T>(fine, coarse, xc, xf, nch, s);
+  if (fine.dim == D && coarse.k == K) return prolong_dk<D, K, T>(fine, coarse, xc, xf, nch, s);
   NNMG_P(2, 1) NNMG_P(2, 2) NNMG_P(2, 3) NNMG_P(2, 4)
   NNMG_P(3, 1) NNMG_P(3, 2) NNMG_P(3, 3) NNMG_P(3, 4)
 #undef NNMG_P
@@ -292,7 +296,7 @@ cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const 
   if (coarse.n_cells == 0) return cudaSuccess;
   const int nch = fine.ncomp * nrhs;
 #define NNMG_R(D, K) \
-  if (fine.dim == D && fine.k == K) return restrict_dk<D, K, T>(fine, coarse, rf, rc, scratch, nch, s);
+  if (fine.dim == D && coarse.k == K) return restrict_dk<D, K, T>(fine, coarse, rf, rc, scratch, nch, s);
   NNMG_R(2, 1) NNMG_R(2, 2) NNMG_R(2, 3) NNMG_R(2, 4)
   NNMG_R(3, 1) NNMG_R(3, 2) NNMG_R(3, 3) NNMG_R(3, 4)
 #undef NNMG_R

@@ -341,6 +341,17 @@ __global__ void __launch_bounds__(kDotThreads) dotw_kernel(const double* __restr
   block_store_partials(v, 1, partial);
 }
 
+// hl[2i] + hl[2i+1] = a[i] to about 2^-48 relative (double-word split)
+__global__ void split_dw_kernel(const double* __restrict__ a, float* __restrict__ hl, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    const float h = __double2float_rn(v);
+    hl[2 * i] = h;
+    hl[2 * i + 1] = __double2float_rn(v - (double)h);
+  }
+}
+
 __global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y,
                             double sy, int64_t n) {
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n;
@@ -453,6 +464,11 @@ cudaError_t launch_dot_weighted(const double* a, const double* b, const double* 
                                 double* partial, int64_t rows, cudaStream_t s) {
   if (too_big(rows)) return cudaErrorInvalidValue;
   dotw_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, wgt, partial, rows);
+  return cudaGetLastError();
+}
+cudaError_t launch_split_dw(const double* a, float* hl, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  split_dw_kernel<<<vblocks(n), 256, 0, s>>>(a, hl, n);
   return cudaGetLastError();
 }
 cudaError_t launch_axpy(double a, const double* x, double* y, double sy, int64_t rows,

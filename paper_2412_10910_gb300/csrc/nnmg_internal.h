@@ -102,6 +102,7 @@ struct DevLevel {
   int32_t* owner_local = nullptr;    // [n_nodes]
   double* metric64 = nullptr;        // [nc][nmetric][nloc]
   float* metric32 = nullptr;
+  float* metric_dw = nullptr;        // double-word pairs (hi, lo) [nc][nmetric][nloc][2], on demand
   double* diag64 = nullptr;          // [rows] (0 at constrained rows)
   double* dinv64 = nullptr;          // [rows] (0 at constrained rows)
   float* dinv32 = nullptr;
@@ -144,6 +145,11 @@ cudaError_t launch_locate(const DevLevel& coarse, const double* points, const in
 template <typename T>
 cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, double lambda,
                             double mu, cudaStream_t s, int units = 0);
+// y = A x with FP64 vectors and double-word arithmetic on the FP32 pipes
+// (needs L.metric_dw).
+cudaError_t launch_operator_dw(const DevLevel& L, const double* x, double* y, int nrhs,
+                               double lambda, double mu, cudaStream_t s, int units = 0);
+cudaError_t launch_split_dw(const double* a, float* hl, int64_t n, cudaStream_t s);
 // Legal units-per-block choices of the operator kernel for this level (for the
 // autotuner); returns how many were written to out.
 template <typename T>

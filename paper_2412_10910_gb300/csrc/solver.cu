@@ -120,6 +120,18 @@ int ensure_work(nnmg_handle* h) {
   return NNMG_OK;
 }
 
+// Double-word copies of the metric terms, made on first use of the
+// double-word operator.
+int ensure_dw(nnmg_handle* h, int level) {
+  DevLevel& L = h->lv[level];
+  if (L.metric_dw) return NNMG_OK;
+  const size_t nm = (size_t)L.n_cells * L.nmetric * L.nloc;
+  CK(dalloc(h, &L.metric_dw, 2 * nm));
+  CK(launch_split_dw(L.metric64, L.metric_dw, (int64_t)nm, 0));
+  CK(cudaStreamSynchronize(0));
+  return NNMG_OK;
+}
+
 int ensure_pcg(nnmg_handle* h) {
   if (h->pcg_ready) return NNMG_OK;
   const DevLevel& L = h->lv.back();
@@ -182,6 +194,55 @@ int op_units(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
       }
     }
     cudaGetLastError();  // a rejected candidate must not leave a sticky launch error
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (x) cudaFree(x);
+    if (y) cudaFree(y);
+  }
+  h->op_units[key] = best;
+  return best;
+}
+
+// Same as op_units for the double-word operator (FP64 vectors).
+int op_units_dw(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
+  auto key = std::make_tuple(level, (int)NNMG_F64_DW, nrhs);
+  auto it = h->op_units.find(key);
+  if (it != h->op_units.end()) return it->second;
+  static const bool enabled = [] {
+    const char* e = getenv("NNMG_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!enabled || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return 0;
+  const DevLevel& L = h->lv[level];
+  int cand[8];
+  const int nc = operator_unit_candidates<double>(L, nrhs, cand, 8);
+  int best = 0;
+  if (nc > 1 && L.n_cells > 0) {
+    double *x = nullptr, *y = nullptr;
+    const size_t n = (size_t)L.rows * nrhs;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&x, n * sizeof(double)) == cudaSuccess &&
+        cudaMalloc(&y, n * sizeof(double)) == cudaSuccess &&
+        cudaMemsetAsync(x, 0, n * sizeof(double), s) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+      float best_ms = 1e30f;
+      for (int c = 0; c < nc; ++c) {
+        if (cand[c] <= 0) continue;
+        bool ok = launch_operator_dw(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, cand[c]) == cudaSuccess;
+        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+        for (int r = 0; r < 3 && ok; ++r)
+          ok = launch_operator_dw(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, cand[c]) == cudaSuccess;
+        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.f;
+        if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best = cand[c];
+        }
+      }
+    }
+    cudaGetLastError();
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (x) cudaFree(x);
@@ -262,7 +323,7 @@ cudaError_t enqueue_pcg_iter(nnmg_handle* h, int mode, int nrhs, cudaStream_t s)
   const int top = (int)h->lv.size() - 1;
   const int64_t rows = L.rows;
   cudaError_t e;
-  if (mode == NNMG_FP32_MG_FP64_CG) {
+  if (mode == NNMG_FP32_MG_FP64_CG || mode == NNMG_FP32_MG_DW_CG) {
     e = launch_cast<double, float>(h->pr, h->w32.f[top], rows * nrhs, s);
     if (e != cudaSuccess) return e;
     e = enqueue_vcycle<float>(h, h->w32.f[top], nrhs, s);
@@ -277,9 +338,13 @@ cudaError_t enqueue_pcg_iter(nnmg_handle* h, int mode, int nrhs, cudaStream_t s)
     if ((e = launch_dot_partial<double>(h->pr, z, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
     if ((e = launch_pcg_beta_p<double>(h->sc, h->partial, z, h->pp, rows, nrhs, s)) != cudaSuccess) return e;
   }
-  if ((e = launch_operator<double>(L, h->pp, h->pq, nrhs, h->opt.lambda, h->opt.mu, s,
-                                   op_units<double>(h, top, nrhs, s))) != cudaSuccess)
-    return e;
+  if (mode == NNMG_FP32_MG_DW_CG)
+    e = launch_operator_dw(L, h->pp, h->pq, nrhs, h->opt.lambda, h->opt.mu, s,
+                           op_units_dw(h, top, nrhs, s));
+  else
+    e = launch_operator<double>(L, h->pp, h->pq, nrhs, h->opt.lambda, h->opt.mu, s,
+                                op_units<double>(h, top, nrhs, s));
+  if (e != cudaSuccess) return e;
   if ((e = launch_dot_partial<double>(h->pp, h->pq, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
   if ((e = launch_pcg_alpha(h->sc, h->partial, nrhs, s)) != cudaSuccess) return e;
   if ((e = launch_pcg_update(h->sc, h->pp, h->pq, h->px, h->pr, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
@@ -478,8 +543,8 @@ int setup_coarse(nnmg_handle* h, DevLevel& L, cudaStream_t s) {
 int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStream_t s) {
   const nnmg_options& o = h->opt;
   L.dim = d.dim;
-  L.k = o.degree;
-  L.n1 = o.degree + 1;
+  L.k = d.degree > 0 ? d.degree : o.degree;
+  L.n1 = L.k + 1;
   L.nloc = d.dim == 2 ? L.n1 * L.n1 : L.n1 * L.n1 * L.n1;
   L.ncomp = o.n_components;
   L.nmetric = o.n_components == 1 ? d.dim * (d.dim + 1) / 2 : d.dim * d.dim;
@@ -492,7 +557,7 @@ int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStrea
       return NNMG_INVALID_ARG;
     }
   }
-  int rc = number_nodes(d.cells, d.n_cells, d.n_vertices, d.dim, o.degree, d.dirichlet_vertex, &L.num);
+  int rc = number_nodes(d.cells, d.n_cells, d.n_vertices, d.dim, L.k, d.dirichlet_vertex, &L.num);
   if (rc != NNMG_OK) return rc;
   L.n_nodes = L.num.n_nodes;
   L.rows = L.n_nodes * L.ncomp;
@@ -638,7 +703,7 @@ int setup_gather(nnmg_handle* h, DevLevel& C) {
   return NNMG_OK;
 }
 
-int check_vec_args(nnmg_handle* h, int level, int precision, int nrhs) {
+int check_vec_args(nnmg_handle* h, int level, int precision, int nrhs, bool allow_dw = false) {
   if (!h) {
     set_error("null handle");
     return NNMG_INVALID_ARG;
@@ -647,8 +712,8 @@ int check_vec_args(nnmg_handle* h, int level, int precision, int nrhs) {
     set_error("level out of range");
     return NNMG_INVALID_ARG;
   }
-  if (precision != NNMG_F32 && precision != NNMG_F64) {
-    set_error("precision must be NNMG_F32 or NNMG_F64");
+  if (precision != NNMG_F32 && precision != NNMG_F64 && !(allow_dw && precision == NNMG_F64_DW)) {
+    set_error("precision must be NNMG_F32 or NNMG_F64 (or NNMG_F64_DW for the operator)");
     return NNMG_INVALID_ARG;
   }
   if (nrhs < 1 || nrhs > h->opt.max_nrhs) {
@@ -714,7 +779,8 @@ int nnmg_setup_hierarchy(const nnmg_level_desc* levels, int n_levels, const nnmg
   for (int l = 0; l < n_levels; ++l) {
     const nnmg_level_desc& d = levels[l];
     if ((d.dim != 2 && d.dim != 3) || d.dim != levels[0].dim || d.n_cells < 1 || d.n_vertices < 1 ||
-        !d.vertices || !d.cells || (opt->n_components == 3 && d.dim != 3)) {
+        !d.vertices || !d.cells || (opt->n_components == 3 && d.dim != 3) || d.degree < 0 ||
+        d.degree > kMaxDegree) {
       set_error("invalid level description");
       return NNMG_INVALID_ARG;
     }
@@ -886,7 +952,7 @@ int nnmg_load_vector(nnmg_handle* h, int level, const double* f, int f_per_qp, d
 
 int nnmg_apply_operator(nnmg_handle* h, int level, int precision, const void* x, void* y,
                         int nrhs, void* stream) {
-  int rc = check_vec_args(h, level, precision, nrhs);
+  int rc = check_vec_args(h, level, precision, nrhs, true);
   if (rc) return rc;
   if (!x || !y || x == y) {
     set_error("x and y must be distinct device vectors");
@@ -895,6 +961,13 @@ int nnmg_apply_operator(nnmg_handle* h, int level, int precision, const void* x,
   cudaStream_t s = (cudaStream_t)stream;
   const DevLevel& L = h->lv[level];
   const size_t ts = precision == NNMG_F64 ? sizeof(double) : sizeof(float);
+  if (precision == NNMG_F64_DW) {
+    if ((rc = ensure_dw(h, level))) return rc;
+    const int ou = op_units_dw(h, level, nrhs, s);
+    NNMG_CUDA(cudaMemsetAsync(y, 0, (size_t)L.rows * nrhs * sizeof(double), s));
+    NNMG_CUDA(launch_operator_dw(L, (const double*)x, (double*)y, nrhs, h->opt.lambda, h->opt.mu, s, ou));
+    return NNMG_OK;
+  }
   const int ou = precision == NNMG_F64 ? op_units<double>(h, level, nrhs, s)
                                         : op_units<float>(h, level, nrhs, s);
   NNMG_CUDA(cudaMemsetAsync(y, 0, (size_t)L.rows * nrhs * ts, s));
@@ -984,13 +1057,15 @@ int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
 int nnmg_batch_reset(nnmg_handle* h, int mode, int nslots, double rtol, int maxit, void* stream) {
   int rc = check_vec_args(h, 0, NNMG_F64, nslots);
   if (rc) return rc;
-  if ((mode != NNMG_FP64_MG && mode != NNMG_FP32_MG_FP64_CG) || !(rtol > 0.0) || maxit < 1) {
+  if ((mode != NNMG_FP64_MG && mode != NNMG_FP32_MG_FP64_CG && mode != NNMG_FP32_MG_DW_CG) ||
+      !(rtol > 0.0) || maxit < 1) {
     set_error("bad mode, rtol or maxit");
     return NNMG_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = ensure_pcg(h))) return rc;
-  if ((rc = (mode == NNMG_FP32_MG_FP64_CG ? ensure_work<float>(h) : ensure_work<double>(h)))) return rc;
+  if ((rc = (mode == NNMG_FP64_MG ? ensure_work<double>(h) : ensure_work<float>(h)))) return rc;
+  if (mode == NNMG_FP32_MG_DW_CG && (rc = ensure_dw(h, (int)h->lv.size() - 1))) return rc;
   if (!h->batch_ev) NNMG_CUDA(cudaEventCreateWithFlags(&h->batch_ev, cudaEventDisableTiming));
   const size_t n = (size_t)h->lv.back().rows * nslots * sizeof(double);
   NNMG_CUDA(cudaMemsetAsync(h->px, 0, n, s));
@@ -1088,7 +1163,8 @@ int pcg_run(nnmg_handle* h, int mode, const double* b, int nrhs, double rtol, in
             int* iters_out, double* relres_out, cudaStream_t s) {
   int rc;
   if ((rc = ensure_pcg(h))) return rc;
-  if ((rc = (mode == NNMG_FP32_MG_FP64_CG ? ensure_work<float>(h) : ensure_work<double>(h)))) return rc;
+  if ((rc = (mode == NNMG_FP64_MG ? ensure_work<double>(h) : ensure_work<float>(h)))) return rc;
+  if (mode == NNMG_FP32_MG_DW_CG && (rc = ensure_dw(h, (int)h->lv.size() - 1))) return rc;
   const DevLevel& L = h->lv.back();
   NNMG_CUDA(launch_pcg_init(b, L.row_free, h->pr, h->px, h->pp, h->partial, L.rows, nrhs, s));
   NNMG_CUDA(launch_pcg_start(h->sc, h->partial, nrhs, rtol, maxit, s));
@@ -1126,7 +1202,8 @@ int pcg_run(nnmg_handle* h, int mode, const double* b, int nrhs, double rtol, in
 int pcg_args(nnmg_handle* h, int mode, int nrhs, double rtol, int maxit) {
   int rc = check_vec_args(h, 0, NNMG_F64, nrhs);
   if (rc) return rc;
-  if ((mode != NNMG_FP64_MG && mode != NNMG_FP32_MG_FP64_CG) || !(rtol > 0.0) || maxit < 1) {
+  if ((mode != NNMG_FP64_MG && mode != NNMG_FP32_MG_FP64_CG && mode != NNMG_FP32_MG_DW_CG) ||
+      !(rtol > 0.0) || maxit < 1) {
     set_error("bad mode, rtol or maxit");
     return NNMG_INVALID_ARG;
   }

@@ -67,8 +67,10 @@ def nnmg_default_options():
 
 def nnmg_setup_hierarchy(levels, degree, n_components=1, lame=(1.0, 1.0), cheb_degree=3,
                          smoothing_range=20.0, lanczos_steps=12, eig_safety=1.2, max_nrhs=16,
-                         stream=None):
-    """levels: sequence with .dim, .vertices [nv,dim] f64, .cells [nc,2^dim] i32, .dirichlet [nv] u8."""
+                         stream=None, level_degrees=None):
+    """levels: sequence with .dim, .vertices [nv,dim] f64, .cells [nc,2^dim] i32, .dirichlet [nv] u8.
+
+    level_degrees: optional per-level degrees (0 = `degree`), coarse -> fine."""
     keep = []
     descs = (_abi.LevelDesc * len(levels))()
     for i, lv in enumerate(levels):
@@ -77,7 +79,8 @@ def nnmg_setup_hierarchy(levels, degree, n_components=1, lame=(1.0, 1.0), cheb_d
         dm = None if lv.dirichlet is None else np.ascontiguousarray(lv.dirichlet, dtype=np.uint8)
         keep += [v, c, dm]
         descs[i] = _abi.LevelDesc(int(lv.dim), v.shape[0], v.ctypes.data, c.shape[0], c.ctypes.data,
-                                  None if dm is None else dm.ctypes.data)
+                                  None if dm is None else dm.ctypes.data,
+                                  int(level_degrees[i]) if level_degrees else 0)
     o = nnmg_default_options()
     o.degree, o.n_components = int(degree), int(n_components)
     o.lam, o.mu = float(lame[0]), float(lame[1])
@@ -173,9 +176,15 @@ def _need(h, level, t, nrhs, ncomp, name):
         raise ValueError(f"{name} must hold rows*nrhs = {n.value * ncomp * nrhs} values")
 
 
-def nnmg_apply_operator(h, level, x, y, nrhs, stream=None, ncomp=1):
+def nnmg_apply_operator(h, level, x, y, nrhs, stream=None, ncomp=1, double_word=False):
+    """y = A_l x; double_word=True (FP64 vectors) computes in double-word arithmetic."""
     _need(h, level, x, nrhs, ncomp, "x")
-    _check(_lib.nnmg_apply_operator(h, level, _prec(x), _dev(x, name="x"),
+    prec = _prec(x)
+    if double_word:
+        if prec != _abi.F64:
+            raise ValueError("double-word operator takes float64 vectors")
+        prec = _abi.F64_DW
+    _check(_lib.nnmg_apply_operator(h, level, prec, _dev(x, name="x"),
                                     _dev(y, x.dtype, x.numel(), name="y"), nrhs, _stream(stream)),
            "nnmg_apply_operator")
 
@@ -259,13 +268,14 @@ class Hierarchy:
     """Owner of one device hierarchy; methods forward to the functions above."""
 
     def __init__(self, levels, degree, n_components=1, lame=(1.0, 1.0), cheb_degree=3,
-                 max_nrhs=16, **kw):
+                 max_nrhs=16, level_degrees=None, **kw):
         self.dim = int(levels[0].dim)
         self.degree = int(degree)
         self.ncomp = int(n_components)
+        self.degrees = [int(d) if d else int(degree) for d in (level_degrees or [0] * len(levels))]
         self.nloc = (degree + 1) ** self.dim
         self.h = nnmg_setup_hierarchy(levels, degree, n_components, lame, cheb_degree,
-                                      max_nrhs=max_nrhs, **kw)
+                                      max_nrhs=max_nrhs, level_degrees=level_degrees, **kw)
         self.n_levels = nnmg_n_levels(self.h)
 
     def close(self):
@@ -300,10 +310,10 @@ class Hierarchy:
         return nnmg_constrained_nodes(self.h, level).astype(bool)
 
     def cell_nodes(self, level):
-        return nnmg_cell_nodes(self.h, level, self.nloc)
+        return nnmg_cell_nodes(self.h, level, (self.degrees[level] + 1) ** self.dim)
 
     def quadrature_points(self, level):
-        return nnmg_quadrature_points(self.h, level, self.nloc, self.dim)
+        return nnmg_quadrature_points(self.h, level, (self.degrees[level] + 1) ** self.dim, self.dim)
 
     def transfer_points(self, fine_level):
         return nnmg_transfer_points(self.h, fine_level, self.dim)
@@ -314,8 +324,9 @@ class Hierarchy:
     def load_vector(self, level, f, b, col=0, per_qp=False):
         nnmg_load_vector(self.h, level, f, per_qp, b, self._nrhs(b), col, ncomp=self.ncomp)
 
-    def apply(self, level, x, y):
-        nnmg_apply_operator(self.h, level, x, y, self._nrhs(x), ncomp=self.ncomp)
+    def apply(self, level, x, y, double_word=False):
+        nnmg_apply_operator(self.h, level, x, y, self._nrhs(x), ncomp=self.ncomp,
+                            double_word=double_word)
 
     def prolongate(self, fine_level, xc, xf):
         nnmg_prolongate(self.h, fine_level, xc, xf, self._nrhs(xc), ncomp=self.ncomp)

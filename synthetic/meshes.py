@@ -173,3 +173,43 @@ def family_levels(dim, cells_fine, n_levels, alpha, seed, lengths=None,
         ns.append(max(1, int((ns[-1] - 1) // ratio)))
     ns = ns[::-1]
     return [_level((n,) * dim, lengths, alpha, seed + i, dirichlet) for i, n in enumerate(ns)]
+
+
+def annulus_level(n_r, n_t, r0=0.5, r1=1.0, alpha=0.1, seed=0, n_z=0, height=1.0):
+    """Quad (n_z = 0) or hex mesh of the annulus r0 <= r <= r1 (times [0, height]).
+
+    Vertices on the circles r = r0 and r = r1 lie exactly on them; the cells are
+    Q1, so each level's boundary is a different polygon inscribed in the
+    circles: fine boundary points fall outside coarser levels.  Interior
+    vertices are jittered in (r, theta) by +-alpha of the spacing (splitmix64,
+    one draw per coordinate per vertex).  Dirichlet flags mark r = r0.
+    """
+    nr1 = n_r + 1
+    r = np.linspace(r0, r1, nr1)
+    t = np.linspace(0.0, 2 * np.pi, n_t + 1)[:-1]
+    nz1 = n_z + 1 if n_z else 1
+    z = np.linspace(0.0, height, nz1) if n_z else np.zeros(1)
+    R, T, Z = np.meshgrid(r, t, z, indexing="ij")
+    R, T, Z = (a.ravel(order="F") for a in (R, T, Z))
+    draws = uniform_pm1(seed, 3 * R.size).reshape(R.size, 3)
+    interior_r = (R > r0) & (R < r1)
+    R = np.where(interior_r, R + alpha * (r1 - r0) / n_r * draws[:, 0], R)
+    T = T + alpha * (2 * np.pi / n_t) * draws[:, 1]
+    if n_z:
+        iz = (Z > 0) & (Z < height)
+        Z = np.where(iz, Z + alpha * height / n_z * draws[:, 2], Z)
+    idx = np.arange(R.size).reshape((nr1, n_t, nz1), order="F")
+    cells = []
+    for k in range(max(n_z, 1)):
+        for j in range(n_t):
+            for i in range(n_r):
+                jp = (j + 1) % n_t
+                c = [idx[i, j, k], idx[i + 1, j, k], idx[i, jp, k], idx[i + 1, jp, k]]
+                if n_z:
+                    c += [idx[i, j, k + 1], idx[i + 1, j, k + 1], idx[i, jp, k + 1], idx[i + 1, jp, k + 1]]
+                cells.append(c)
+    cells = np.array(cells, dtype=np.int32)
+    xy = np.stack([R * np.cos(T), R * np.sin(T)] + ([Z] if n_z else []), axis=1)
+    dirichlet = (np.abs(R - r0) < 1e-14).astype(np.uint8)
+    dim = 3 if n_z else 2
+    return Level(dim, np.ascontiguousarray(xy), cells, dirichlet, (n_r, n_t) + ((n_z,) if n_z else ()))

@@ -5,7 +5,7 @@ import functools
 import numpy as np
 
 from synthetic import config_levels
-from synthetic.meshes import CONFIGS
+from synthetic.meshes import CONFIGS, annulus_level
 from tests.oracle_meshes import box_level, scramble
 
 # name -> (levels factory, degree, ncomp, lame, cheb, nrhs)
@@ -21,21 +21,36 @@ CASES = {
     "scrambled_q3": (lambda: [scramble(box_level((2, 2, 2), alpha=0.1, seed=3), 5),
                               scramble(box_level((5, 4, 3), alpha=0.2, seed=4), 6)], 3, 1,
                      (1.0, 1.0), 3, 2),
+    # curved domains with a Neumann outer boundary (Sec. 3.3): fine points outside
+    # the coarser polygonal boundaries go through the nearest-point projection
+    "annulus_q2": (lambda: [annulus_level(2, 12, seed=1), annulus_level(5, 27, seed=2),
+                            annulus_level(11, 57, seed=3)], 2, 1, (1.0, 1.0), 3, 2),
+    "cylinder_q2": (lambda: [annulus_level(2, 8, n_z=2, seed=4), annulus_level(4, 17, n_z=4, seed=5)],
+                    2, 1, (1.0, 1.0), 3, 1),
+    # polynomial coarsening on the coarsest mesh below the non-nested levels
+    "c3_q4_pmg": (lambda: [config_levels("c3_3d_q4_deformed", n_levels=1)[0]] * 4
+                  + config_levels("c3_3d_q4_deformed", n_levels=2)[1:], 4, 1, (1.0, 1.0), 5, 4,
+                  [1, 2, 3, 4, 4]),
 }
+
+
+def degrees(name):
+    c = CASES[name]
+    return c[6] if len(c) > 6 else None
 
 
 @functools.lru_cache(maxsize=None)
 def oracle_case(name):
     from oracle.hierarchy import OracleHierarchy
-    lv, k, nc, lame, cheb, nrhs = CASES[name]
+    lv, k, nc, lame, cheb, nrhs = CASES[name][:6]
     levels = lv()
-    return levels, OracleHierarchy(levels, k, nc, lame, cheb)
+    return levels, OracleHierarchy(levels, k, nc, lame, cheb, level_degrees=degrees(name))
 
 
 def gpu_case(name, levels):
     from paper_2412_10910_gb300 import nnmg
-    _, k, nc, lame, cheb, nrhs = CASES[name]
-    return nnmg.Hierarchy(levels, k, nc, lame, cheb, max_nrhs=16)
+    _, k, nc, lame, cheb, nrhs = CASES[name][:6]
+    return nnmg.Hierarchy(levels, k, nc, lame, cheb, max_nrhs=16, level_degrees=degrees(name))
 
 
 def rng_vec(rows, nrhs, seed):

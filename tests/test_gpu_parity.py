@@ -49,11 +49,13 @@ def test_point_location(case):
         np.testing.assert_allclose(xi, oxi, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5), ("dw", 1e-12)])
 def test_operator(case, dtype, tol):
+    """dw: FP64 vectors, double-word arithmetic (about 2^-48 per operation), held
+    to the FP64 tolerance."""
     name, levels, O, H = case
     nrhs = CASES[name][5]
-    tdt = torch.float64 if dtype == "f64" else torch.float32
+    tdt = torch.float32 if dtype == "f32" else torch.float64
     for l in range(len(O.levels)):
         x = rng_vec(O.levels[l].n, nrhs, 10 + l)
         xo = x.copy()
@@ -61,7 +63,7 @@ def test_operator(case, dtype, tol):
         yo = O.apply(l, xo)
         xt = torch.tensor(x, dtype=tdt, device="cuda")
         y = torch.full_like(xt, 7.0)
-        H.apply(l, xt, y)
+        H.apply(l, xt, y, double_word=(dtype == "dw"))
         assert _relmax(y.double().cpu().numpy(), yo) <= tol, (l, _relmax(y.double().cpu().numpy(), yo))
 
 
@@ -125,7 +127,7 @@ def test_vcycle(case):
     assert _relmax(z2.cpu().numpy(), zo) <= 1e-9
 
 
-@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+@pytest.mark.parametrize("mode", ["fp32", "fp64", "dw"])
 def test_pcg(case, mode):
     from paper_2412_10910_gb300 import _abi
     name, levels, O, H = case
@@ -135,10 +137,10 @@ def test_pcg(case, mode):
     b = rng_vec(n, nrhs, 50)
     b[np.repeat(O.levels[top].constrained, O.ncomp)] = 0.0
     xo64, its64, _, _ = O.pcg(b, "fp64", rtol=1e-8)
-    _, itso, _, _ = O.pcg(b, mode, rtol=1e-8)
+    _, itso, _, _ = O.pcg(b, "fp32" if mode == "dw" else mode, rtol=1e-8)
     bt = torch.tensor(b, device="cuda")
     x = H.vector(top, nrhs)
-    m = _abi.FP32_MG_FP64_CG if mode == "fp32" else _abi.FP64_MG
+    m = {"fp32": _abi.FP32_MG_FP64_CG, "fp64": _abi.FP64_MG, "dw": _abi.FP32_MG_DW_CG}[mode]
     for rep in range(2):                       # eager first call, graph replay second
         st, its, rel = H.pcg(bt, x, mode=m, rtol=1e-8, maxit=100)
         assert st == 0 and np.all(rel <= 1e-8)

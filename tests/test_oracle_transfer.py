@@ -130,3 +130,47 @@ def test_located_points_are_true_preimages_in_distorted_cells():
     p = pts[np.argmin(np.linalg.norm(pts - np.array([0.26927729, 0.71235964, 0.08251205]), axis=1))]
     _, conv = transfer.newton_inverse(p[None], c_lv.vertices[c_lv.cells[[8]]], 3)
     assert not conv[0]
+
+
+@pytest.mark.parametrize("dim,kc,kf", [(2, 1, 2), (2, 3, 4), (3, 1, 2), (3, 2, 3)])
+def test_degree_change_on_one_mesh_is_the_canonical_embedding(dim, kc, kf):
+    """Polynomial coarsening (Sec. 2, "Coarse grid solvers"): on one mesh Q_kc is
+    contained in Q_kf, so P interpolates the coarse field exactly at every point."""
+    lv = box_level((3,) * dim, alpha=0.2, seed=2, dirichlet="none")
+    c = _level(lv, kc)
+    f = _level(lv, kf)
+    P, free_f, cell, xi = _P(f, c, kc, dim)
+    rng = np.random.default_rng(4)
+    uc = rng.standard_normal(c["n"])
+    uf = P @ uc
+    xr = rng.random((7, dim))
+    vf, _ = fe.tensor_basis(kf, dim, xr)
+    vc, _ = fe.tensor_basis(kc, dim, xr)
+    for K in range(len(lv.cells)):
+        np.testing.assert_allclose(vf @ uf[f["node_of"][K]], vc @ uc[c["node_of"][K]], atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_curved_boundary_points_are_projected(k):
+    """Annulus levels meshed independently (Sec. 3.3): fine Neumann points on the
+    outer circle lie outside the coarse polygon; they are assigned the nearest
+    coarse cell with xi projected onto the reference cell.  P keeps the
+    partition of unity there, and the projected point is within the gap
+    between the polygons (O(h^2))."""
+    from synthetic.meshes import annulus_level
+    c_lv, f_lv = annulus_level(3, 10, seed=1), annulus_level(7, 23, seed=2)
+    c = _level(c_lv, k)
+    f = _level(f_lv, k)
+    P, free_f, cell, xi = _P(f, c, k, 2)
+    pts = f["pts"][free_f]
+    # partition of unity where the coarse cell has no Dirichlet (dropped) nodes:
+    # the outer ring of the coarse mesh, r > 5/6
+    outer = np.linalg.norm(pts, axis=1) > 0.85
+    np.testing.assert_allclose((P @ np.ones(P.shape[1]))[outer], 1.0, atol=1e-12)
+    N, _ = fe.q1_shape(2, xi)
+    mapped = np.einsum("pv,pvd->pd", N, c["vertices"][c["cells"][cell]])
+    r = np.linalg.norm(pts, axis=1)
+    outside = np.linalg.norm(mapped - pts, axis=1) > 1e-12
+    assert outside.sum() > 0 and np.all(r[outside] > 0.9)          # only near the outer circle
+    h = 2 * np.pi / 10
+    assert np.max(np.linalg.norm(mapped - pts, axis=1)) < h * h
