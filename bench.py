@@ -253,6 +253,68 @@ def run_configs(args, rank):
         if rank == 0:
             print(json.dumps(out), flush=True)
         H.close()
+    run_nested_cube(args, rank)
+
+
+def run_nested_cube(args, rank):
+    """The paper's nested cube (Sec. 5 comparison of global coarsening and the
+    non-nested transfer): [-1,1]^3, Q4, levels 2^3 .. 32^3 cells by global
+    refinement, f = 1.  Same hierarchy solved with the non-nested point
+    evaluation and with the nested sum-factorized transfer."""
+    import numpy as np
+    import torch
+    from paper_2412_10910_gb300 import _abi, nnmg
+    from synthetic.meshes import Level, boundary_vertex_mask, refine_nested, structured_grid
+
+    v, c = structured_grid((2, 2, 2), (2.0, 2.0, 2.0))
+    lv = [Level(3, v - 1.0, c, boundary_vertex_mask(v, (2.0, 2.0, 2.0)).astype(np.uint8), (2, 2, 2))]
+    par = [None]
+    for _ in range(4):
+        f, p_, c_ = refine_nested(lv[-1])
+        lv.append(f)
+        par.append((p_, c_))
+    H = nnmg.Hierarchy(lv, 4, cheb_degree=3, max_nrhs=16)
+    top = len(lv) - 1
+    nn_, nfree, _ = H.info(top)
+    b = H.vector(top, 1)
+    H.load_vector(top, np.ones(1), b, col=0)
+    x = torch.zeros_like(b)
+    out = {"config": "nested_cube_q4 (paper Sec. 5 cube, levels 2^3..32^3)", "fine_free_dofs": nfree}
+    for tag in ("non_nested", "nested_gc"):
+        for l in range(1, len(lv)):
+            H.set_nested(l, *(par[l] if tag == "nested_gc" else (None, None)))
+        for _ in range(3):
+            st, its, rel = H.pcg(b, x)
+        ts = []
+        for _ in range(max(5, args.steps // 2)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st, its, rel = H.pcg(b, x)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ts.sort()
+        xc = torch.randn(H.rows(top - 1), 1, dtype=torch.float32, device="cuda")
+        xf = H.vector(top, 1, torch.float32)
+        rc = H.vector(top - 1, 1, torch.float32)
+        tr = []
+        for i in range(13):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            H.prolongate(top, xc, xf)
+            e1.record()
+            H.restrict(top, xf, rc)
+            e2.record()
+            torch.cuda.synchronize()
+            if i >= 3:
+                tr.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+        out[tag] = {"solve_p50_ms": ts[len(ts) // 2], "iterations": [int(i) for i in its],
+                    "max_relres": float(max(rel)),
+                    "finest_prolongation_ms": statistics.median(t[0] for t in tr),
+                    "finest_restriction_ms": statistics.median(t[1] for t in tr)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    H.close()
 
 
 def run_serving(args, rank):
@@ -310,8 +372,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["solve", "solve64", "vcycle", "op64", "op32", "serving",
-                                       "configs"],
+    ap.add_argument("--only", choices=["solve", "solve64", "solvedw", "vcycle", "op64", "op32",
+                                       "opdw", "serving", "configs"],
                     default=None, help="run only one timed section (for profiler launch lists), "
                     "or the serving mix")
     ap.add_argument("--requests", type=int, default=2000, help="serving mix: number of requests")
@@ -366,16 +428,17 @@ def main():
         return H.pcg(b, x, mode=mode, rtol=1e-8, maxit=100)
 
     if args.only:
-        fns = {"solve": lambda: solve(_abi.FP32_MG_FP64_CG), "solve64": lambda: solve(_abi.FP64_MG)}
+        fns = {"solve": lambda: solve(_abi.FP32_MG_FP64_CG), "solve64": lambda: solve(_abi.FP64_MG),
+               "solvedw": lambda: solve(_abi.FP32_MG_DW_CG)}
         if args.only in ("vcycle",):
             r32 = torch.randn(rows, nrhs, dtype=torch.float32, device="cuda")
             z32 = torch.empty_like(r32)
             fns["vcycle"] = lambda: H.vcycle(r32, z32)
-        if args.only in ("op64", "op32"):
-            dt = torch.float64 if args.only == "op64" else torch.float32
+        if args.only in ("op64", "op32", "opdw"):
+            dt = torch.float32 if args.only == "op32" else torch.float64
             xo = torch.randn(rows, nrhs, dtype=dt, device="cuda")
             yo = torch.empty_like(xo)
-            fns[args.only] = lambda: H.apply(top, xo, yo)
+            fns[args.only] = lambda: H.apply(top, xo, yo, double_word=(args.only == "opdw"))
         fn = fns[args.only]
         for _ in range(args.warmup):
             fn()

@@ -202,6 +202,19 @@ int nnmg_restrict(nnmg_handle* h, int fine_level, int precision, const void* fin
 int nnmg_restrict_noalloc(nnmg_handle* h, int fine_level, int precision, const void* fine,
                           void* coarse, int nrhs, void* stream);
 
+/* Switch the transfer between fine_level and fine_level-1 to the nested
+ * (global-coarsening) form, the comparison system of the paper's Sec. 5: the
+ * fine mesh must be the uniform 2^d refinement of the coarse one (same
+ * degree, fine cells obtained by mapping the reference sub-cells through the
+ * coarse Q1 map, corner order aligned with the parent).  parent_cell
+ * [n_fine_cells] gives each fine cell's coarse cell, child_index
+ * [n_fine_cells] its position (bit d = upper half in direction d).  The
+ * transfer is then sum-factorized per child (the same operator P as the
+ * point evaluation, evaluated differently).  parent_cell = NULL switches back
+ * to the non-nested transfer.  Captured graphs are dropped. */
+int nnmg_set_nested(nnmg_handle* h, int fine_level, const int32_t* parent_cell,
+                    const uint8_t* child_index);
+
 /* One V-cycle (Algorithm 1) on the finest level from a zero guess: z ~ A_L^-1 r.
  * Chebyshev-Jacobi pre- and post-smoothing, residual, restriction, recursion,
  * prolongation; coarsest level solved directly in FP64. */

@@ -19,6 +19,7 @@
 // share it are summed in ascending (cell, local) order.  No atomics: results
 // are bitwise reproducible.
 #include <algorithm>
+#include <cstring>
 
 #include "nnmg_internal.h"
 
@@ -275,6 +276,186 @@ cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* rc
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------- nested (GC)
+// Transfer between nested levels (the global-coarsening comparison of the
+// paper's Sec. 5): a fine cell that is child b = (b_0, b_1, b_2) of coarse
+// cell c carries u_f = (E_{b_2} x E_{b_1} x E_{b_0}) u_c with the 1D matrices
+// E_b[m][l] = L_l((b + t_m) / 2) (t_m the Gauss-Lobatto nodes): sum
+// factorization, d sweeps of (k+1)^(d+1) FMAs per child.  One block per coarse
+// cell; a fine node is written by the child cell that numbered it first, so
+// each is written once.  Restriction applies the transposed sweeps and adds
+// the children in fixed order into the per-coarse-cell buffer of the
+// non-nested restriction, whose second phase then gathers (deterministic).
+template <typename T>
+struct GcTables {
+  T E[2][kMaxN][kMaxN];
+};
+
+template <int D, int N, typename T>
+__device__ __forceinline__ void gc_sweep(const T (&E)[kMaxN][kMaxN], const T* in, T* out, int dir,
+                                         bool transpose, int nch) {
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  const int stride = dir == 0 ? 1 : (dir == 1 ? N : N * N);
+  for (int e = threadIdx.x; e < NL * nch; e += blockDim.x) {
+    const int i = e / nch, ch = e - i * nch;
+    const int m = (i / stride) % N;
+    const int base = i - m * stride;
+    T v = 0;
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+      v += (transpose ? E[l][m] : E[m][l]) * in[(base + l * stride) * nch + ch];
+    out[e] = v;
+  }
+}
+
+template <int D, int K, typename T>
+__global__ void gc_prolong_kernel(const int32_t* __restrict__ coarse_cell_nodes,
+                                  const T* __restrict__ xc, T* __restrict__ xf,
+                                  const int32_t* __restrict__ children,
+                                  const int32_t* __restrict__ fine_cell_nodes,
+                                  const int32_t* __restrict__ owner_cell,
+                                  const int32_t* __restrict__ owner_local, int nch,
+                                  GcTables<T> G) {
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  extern __shared__ unsigned char smem_raw[];
+  T* u = reinterpret_cast<T*>(smem_raw);  // [NL][nch] coarse values
+  T* a = u + NL * nch;                      // sweep buffers
+  T* b = a + NL * nch;
+  const int64_t c = blockIdx.x;
+  for (int e = threadIdx.x; e < NL * nch; e += blockDim.x) {
+    const int j = e / nch, ch = e - j * nch;
+    const int node = coarse_cell_nodes[c * NL + j];
+    u[e] = node >= 0 ? xc[(int64_t)node * nch + ch] : T(0);
+  }
+  __syncthreads();
+  for (int cb = 0; cb < (1 << D); ++cb) {
+    const int f = children[c * (1 << D) + cb];
+    gc_sweep<D, N, T>(G.E[cb & 1], u, a, 0, false, nch);
+    __syncthreads();
+    gc_sweep<D, N, T>(G.E[(cb >> 1) & 1], a, b, 1, false, nch);
+    __syncthreads();
+    const T* res = b;
+    if constexpr (D == 3) {
+      gc_sweep<D, N, T>(G.E[(cb >> 2) & 1], b, a, 2, false, nch);
+      __syncthreads();
+      res = a;
+    }
+    for (int e = threadIdx.x; e < NL * nch; e += blockDim.x) {
+      const int i = e / nch, ch = e - i * nch;
+      const int node = fine_cell_nodes[(int64_t)f * NL + i];
+      if (node >= 0 && owner_cell[node] == f && owner_local[node] == i)
+        xf[(int64_t)node * nch + ch] += res[e];
+    }
+    __syncthreads();
+  }
+}
+
+template <int D, int K, typename T>
+__global__ void gc_restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
+                                    const int32_t* __restrict__ children,
+                                    const int32_t* __restrict__ fine_cell_nodes,
+                                    const int32_t* __restrict__ owner_cell,
+                                    const int32_t* __restrict__ owner_local, int nch,
+                                    GcTables<T> G) {
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  extern __shared__ unsigned char smem_raw[];
+  T* acc = reinterpret_cast<T*>(smem_raw);  // [NL][nch]
+  T* a = acc + NL * nch;
+  T* b = a + NL * nch;
+  const int64_t c = blockIdx.x;
+  for (int e = threadIdx.x; e < NL * nch; e += blockDim.x) acc[e] = T(0);
+  for (int cb = 0; cb < (1 << D); ++cb) {
+    const int f = children[c * (1 << D) + cb];
+    for (int e = threadIdx.x; e < NL * nch; e += blockDim.x) {
+      const int i = e / nch, ch = e - i * nch;
+      const int node = fine_cell_nodes[(int64_t)f * NL + i];
+      const bool own = node >= 0 && owner_cell[node] == f && owner_local[node] == i;
+      a[e] = own ? rf[(int64_t)node * nch + ch] : T(0);
+    }
+    __syncthreads();
+    T* in = a;
+    T* out = b;
+    if constexpr (D == 3) {
+      gc_sweep<D, N, T>(G.E[(cb >> 2) & 1], in, out, 2, true, nch);
+      __syncthreads();
+      in = b;
+      out = a;
+    }
+    gc_sweep<D, N, T>(G.E[(cb >> 1) & 1], in, out, 1, true, nch);
+    __syncthreads();
+    gc_sweep<D, N, T>(G.E[cb & 1], out, in, 0, true, nch);
+    __syncthreads();
+    for (int e = threadIdx.x; e < NL * nch; e += blockDim.x) acc[e] += in[e];
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NL * nch; e += blockDim.x) buf[(c * NL) * nch + e] = acc[e];
+}
+
+template <typename T>
+GcTables<T> gc_tables(int k) {
+  Basis1D<double> d;
+  Basis1D<float> f;
+  make_basis(k, &d, &f);
+  GcTables<T> g;
+  std::memset(&g, 0, sizeof(g));
+  const int n = k + 1;
+  for (int b = 0; b < 2; ++b)
+    for (int m = 0; m < n; ++m) {
+      const double x = 0.5 * (b + d.gl[m]);
+      for (int l = 0; l < n; ++l) {
+        double v = d.gl_scale[l];
+        for (int q = 0; q < n; ++q)
+          if (q != l) v *= x - d.gl[q];
+        g.E[b][m][l] = (T)v;
+      }
+    }
+  return g;
+}
+
+template <int D, int K, typename T>
+cudaError_t gc_prolong_dk(const DevLevel& f, const DevLevel& c, const T* xc, T* xf, int nch,
+                          cudaStream_t s) {
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  const size_t smem = 3 * (size_t)NL * nch * sizeof(T);
+  auto kern = gc_prolong_kernel<D, K, T>;
+  static size_t smem_set = 48 * 1024;
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
+  kern<<<(unsigned)c.n_cells, 128, smem, s>>>(c.cell_nodes, xc, xf, f.gc_children, f.cell_nodes,
+                                              f.owner_cell, f.owner_local, nch, gc_tables<T>(K));
+  return cudaGetLastError();
+}
+
+template <int D, int K, typename T>
+cudaError_t gc_restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* rc, T* scratch,
+                           int nch, cudaStream_t s) {
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  const size_t smem = 3 * (size_t)NL * nch * sizeof(T);
+  auto kern = gc_restrict1_kernel<D, K, T>;
+  static size_t smem_set = 48 * 1024;
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
+  kern<<<(unsigned)c.n_cells, 128, smem, s>>>(rf, scratch, f.gc_children, f.cell_nodes,
+                                              f.owner_cell, f.owner_local, nch, gc_tables<T>(K));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t n = c.n_nodes * nch;
+  restrict2_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(scratch, c.gather_start,
+                                                                  c.gather_pos, rc, c.n_nodes, nch);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 template <typename T>
@@ -282,6 +463,14 @@ cudaError_t launch_prolongate_add(const DevLevel& fine, const DevLevel& coarse, 
                                   T* xf, int nrhs, cudaStream_t s) {
   if (coarse.n_cells == 0) return cudaSuccess;
   const int nch = fine.ncomp * nrhs;
+  if (fine.gc_active) {
+#define NNMG_G(D, K) \
+  if (fine.dim == D && coarse.k == K) return gc_prolong_dk<D, K, T>(fine, coarse, xc, xf, nch, s);
+    NNMG_G(2, 1) NNMG_G(2, 2) NNMG_G(2, 3) NNMG_G(2, 4)
+    NNMG_G(3, 1) NNMG_G(3, 2) NNMG_G(3, 3) NNMG_G(3, 4)
+#undef NNMG_G
+    return cudaErrorInvalidValue;
+  }
 #define NNMG_P(D, K) \
   if (fine.dim == D && coarse.k == K) return prolong_dk<D, K, T>(fine, coarse, xc, xf, nch, s);
   NNMG_P(2, 1) NNMG_P(2, 2) NNMG_P(2, 3) NNMG_P(2, 4)
@@ -295,6 +484,14 @@ cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const 
                             T* scratch, int nrhs, cudaStream_t s) {
   if (coarse.n_cells == 0) return cudaSuccess;
   const int nch = fine.ncomp * nrhs;
+  if (fine.gc_active) {
+#define NNMG_G(D, K) \
+  if (fine.dim == D && coarse.k == K) return gc_restrict_dk<D, K, T>(fine, coarse, rf, rc, scratch, nch, s);
+    NNMG_G(2, 1) NNMG_G(2, 2) NNMG_G(2, 3) NNMG_G(2, 4)
+    NNMG_G(3, 1) NNMG_G(3, 2) NNMG_G(3, 3) NNMG_G(3, 4)
+#undef NNMG_G
+    return cudaErrorInvalidValue;
+  }
 #define NNMG_R(D, K) \
   if (fine.dim == D && coarse.k == K) return restrict_dk<D, K, T>(fine, coarse, rf, rc, scratch, nch, s);
   NNMG_R(2, 1) NNMG_R(2, 2) NNMG_R(2, 3) NNMG_R(2, 4)

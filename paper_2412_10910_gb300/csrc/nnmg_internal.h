@@ -118,6 +118,10 @@ struct DevLevel {
   int32_t* cell_pt_start = nullptr;  // [n_cells(coarse)+1]
   std::vector<int32_t> h_loc_cell;   // by increasing free fine node
   std::vector<double> h_loc_xi;
+  // nested transfer from the next coarser level (global-coarsening comparison):
+  // children of every coarse cell ordered by child index [n_cells(coarse)][2^d]
+  int32_t* gc_children = nullptr;
+  bool gc_active = false;
   // restriction gather lists of this level as a coarse level
   int32_t* gather_start = nullptr;   // [n_nodes+1]
   int32_t* gather_pos = nullptr;     // [..] cell*nloc + local, ascending

@@ -1053,6 +1053,47 @@ int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
   return NNMG_OK;
 }
 
+// ------------------------------------------------------- nested transfer
+int nnmg_set_nested(nnmg_handle* h, int fine_level, const int32_t* parent_cell,
+                    const uint8_t* child_index) {
+  if (!h || fine_level < 1 || fine_level >= (int)h->lv.size()) {
+    set_error("nnmg_set_nested: bad handle or fine_level");
+    return NNMG_INVALID_ARG;
+  }
+  DevLevel& F = h->lv[fine_level];
+  const DevLevel& C = h->lv[fine_level - 1];
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);   // the V-cycle changes
+  h->graphs.clear();
+  h->runs.clear();
+  if (!parent_cell) {
+    F.gc_active = false;
+    return NNMG_OK;
+  }
+  if (!child_index) {
+    set_error("nnmg_set_nested: child_index is required with parent_cell");
+    return NNMG_INVALID_ARG;
+  }
+  const int nchild = 1 << F.dim;
+  if (F.k != C.k || F.n_cells != C.n_cells * nchild) {
+    set_error("nnmg_set_nested: the fine level must be the 2^d refinement of the coarse one, same degree");
+    return NNMG_INVALID_ARG;
+  }
+  std::vector<int32_t> ch((size_t)C.n_cells * nchild, -1);
+  for (int64_t f = 0; f < F.n_cells; ++f) {
+    const int64_t p = parent_cell[f];
+    const int b = child_index[f];
+    if (p < 0 || p >= C.n_cells || b >= nchild || ch[(size_t)p * nchild + b] >= 0) {
+      set_error("nnmg_set_nested: parent/child lists are not a 2^d refinement");
+      return NNMG_INVALID_ARG;
+    }
+    ch[(size_t)p * nchild + b] = (int32_t)f;
+  }
+  if (!F.gc_children) CK(dalloc(h, &F.gc_children, ch.size()));
+  CK(cudaMemcpy(F.gc_children, ch.data(), ch.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  F.gc_active = true;
+  return NNMG_OK;
+}
+
 // ------------------------------------------------------- continuous batching
 int nnmg_batch_reset(nnmg_handle* h, int mode, int nslots, double rtol, int maxit, void* stream) {
   int rc = check_vec_args(h, 0, NNMG_F64, nslots);

@@ -215,6 +215,16 @@ def nnmg_restrict_noalloc(h, fine_level, fine, coarse, nrhs, stream=None, ncomp=
                                       _stream(stream)), "nnmg_restrict_noalloc")
 
 
+def nnmg_set_nested(h, fine_level, parent_cell=None, child_index=None):
+    """Use the nested (sum-factorized) transfer for this level pair; None to undo."""
+    if parent_cell is None:
+        _check(_lib.nnmg_set_nested(h, fine_level, None, None), "nnmg_set_nested")
+        return
+    p = np.ascontiguousarray(parent_cell, dtype=np.int32)
+    c = np.ascontiguousarray(child_index, dtype=np.uint8)
+    _check(_lib.nnmg_set_nested(h, fine_level, p.ctypes.data, c.ctypes.data), "nnmg_set_nested")
+
+
 def nnmg_vcycle(h, r, z, nrhs, stream=None, ncomp=1):
     _need(h, nnmg_n_levels(h) - 1, r, nrhs, ncomp, "r")
     _check(_lib.nnmg_vcycle(h, _prec(r), _dev(r, name="r"), _dev(z, r.dtype, r.numel(), name="z"),
@@ -333,6 +343,9 @@ class Hierarchy:
 
     def restrict(self, fine_level, rf, rc):
         nnmg_restrict(self.h, fine_level, rf, rc, self._nrhs(rf), ncomp=self.ncomp)
+
+    def set_nested(self, fine_level, parent_cell=None, child_index=None):
+        nnmg_set_nested(self.h, fine_level, parent_cell, child_index)
 
     def vcycle(self, r, z):
         nnmg_vcycle(self.h, r, z, self._nrhs(r), ncomp=self.ncomp)

@@ -213,3 +213,41 @@ def annulus_level(n_r, n_t, r0=0.5, r1=1.0, alpha=0.1, seed=0, n_z=0, height=1.0
     dirichlet = (np.abs(R - r0) < 1e-14).astype(np.uint8)
     dim = 3 if n_z else 2
     return Level(dim, np.ascontiguousarray(xy), cells, dirichlet, (n_r, n_t) + ((n_z,) if n_z else ()))
+
+
+def refine_nested(level: Level):
+    """Uniform refinement of a structured level (from structured_grid, possibly
+    jittered): every cell is split into 2^d children by mapping the reference
+    midpoints through the cell's Q1 map, so the refined space contains the
+    coarse one.  Returns (fine Level, parent cell [n_fine_cells] int32,
+    child index [n_fine_cells] uint8 with bit d = position in direction d)."""
+    n = level.n
+    dim = len(n)
+    nf = tuple(2 * m for m in n)
+    nv_c = [m + 1 for m in n]
+    nv_f = [m + 1 for m in nf]
+    vf = np.empty((int(np.prod(nv_f)), dim))
+    grids = np.meshgrid(*[np.arange(m) for m in nv_f], indexing="ij")
+    I = [g.ravel(order="F") for g in grids]                       # fine vertex multi-index
+    cidx = [np.minimum(I[d] // 2, n[d] - 1) for d in range(dim)]   # a coarse cell containing it
+    eta = [(I[d] - 2 * cidx[d]) / 2.0 for d in range(dim)]         # 0, 1/2 or 1
+    cell = sum(cidx[d] * int(np.prod(n[:d])) for d in range(dim))
+    X = level.vertices[level.cells[cell]]                          # [nv, 2^d, dim]
+    w = np.ones((len(cell), 2 ** dim))
+    for v in range(2 ** dim):
+        for d in range(dim):
+            w[:, v] *= eta[d] if (v >> d) & 1 else 1.0 - eta[d]
+    vf[:] = np.einsum("pv,pvd->pd", w, X)
+    _, cells_f = structured_grid(nf, (1.0,) * dim)
+    cg = np.meshgrid(*[np.arange(m) for m in nf], indexing="ij")
+    J = [g.ravel(order="F") for g in cg]
+    parent = sum((J[d] // 2) * int(np.prod(n[:d])) for d in range(dim)).astype(np.int32)
+    child = sum((J[d] % 2) << d for d in range(dim)).astype(np.uint8)
+    dmask = np.zeros(len(vf), dtype=np.uint8)
+    on = np.zeros(len(vf), dtype=bool)
+    for d in range(dim):
+        on |= (I[d] == 0) | (I[d] == nv_f[d] - 1)
+    # a fine boundary vertex is Dirichlet if its coarse boundary face is
+    if level.dirichlet.any():
+        dmask[on] = 1
+    return Level(dim, vf, cells_f.astype(np.int32), dmask, nf), parent, child
