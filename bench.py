@@ -116,6 +116,15 @@ class Clocks:
         return out
 
 
+def replica_aggregate(local_ms, local_units, world, reduce_max, reduce_sum):
+    """Whole-job numbers of `world` independent replicas: the slowest rank's
+    time and the units all ranks processed (weak scaling, no data exchange).
+    reduce_max / reduce_sum combine one float across ranks."""
+    ms = reduce_max(local_ms) if world > 1 else local_ms
+    units = reduce_sum(local_units) if world > 1 else local_units
+    return ms, units, units / (ms / 1e3)
+
+
 def kernels_per_solve(n_levels, cheb, iters):
     """Kernel launches of one PCG solve: init 2, per iteration the V-cycle
     (per level above the coarsest: 1 + 2(m-1) pre, 2 residual, 2 restriction,
@@ -405,12 +414,16 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
+    def _reduce(v, op):
         t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=op)
         return float(t.item())
+
+    def max_over_ranks(v):
+        return v if world == 1 else _reduce(v, dist.ReduceOp.MAX)
+
+    def sum_over_ranks(v):
+        return v if world == 1 else _reduce(v, dist.ReduceOp.SUM)
 
     cfg = CONFIGS[CONFIG]
     levels = config_levels(CONFIG)
@@ -491,11 +504,12 @@ def main():
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    total_ms = max_over_ranks(ev0.elapsed_time(ev1))
     lat = sorted(e0.elapsed_time(e1) for e0, e1 in per_step)
-    ms = total_ms / args.steps
     dofs = n_free * nrhs
-    value = dofs * world / (ms / 1e3)
+    total_ms, total_units, _ = replica_aggregate(ev0.elapsed_time(ev1), dofs * args.steps, world,
+                                                 max_over_ranks, sum_over_ranks)
+    ms = total_ms / args.steps
+    value = total_units / (total_ms / 1e3)
     relres = [float(r) for r in rel]
 
     # ---- comparator: plain FP64 multigrid

@@ -247,17 +247,20 @@ int nnmg_pcg_solve_host(nnmg_handle* h, int mode, const double* b_host, double* 
  *   column ||r|| <= rtol ||b||) and maxit (per column) as for nnmg_pcg_solve.
  * nnmg_batch_admit: start column `slot` from the FP64 right-hand side b [rows]
  *   (device, or host if b_on_host) with x0 = 0.
- * nnmg_batch_step: enqueue one PCG iteration of all columns (inactive columns
- *   stay frozen) and an asynchronous copy of the per-column state.
+ * nnmg_batch_step: enqueue `iterations` PCG iterations of all columns
+ *   (inactive columns stay frozen; a column that converges stops updating)
+ *   and an asynchronous copy of the per-column state.
  * nnmg_batch_poll: if the last step has finished (or, with wait != 0, after
  *   waiting for it) set *ready = 1 and fill host arrays [nslots] (may be
  *   NULL): active flags, iteration counts, relative residuals and per-column
  *   status (NNMG_OK, NNMG_NOT_CONVERGED, NNMG_BREAKDOWN); else *ready = 0.
- * nnmg_batch_retire: copy column `slot` of x into x [rows] (device, or host if
- *   x_on_host, then synchronising the stream) and mark the slot empty. */
+ * nnmg_batch_retire: enqueue the copy of column `slot` of x into x [rows]
+ *   (device, or host if x_on_host; host memory should be pinned) and mark the
+ *   slot empty.  The copy is asynchronous: read x after synchronising the
+ *   stream or after the next nnmg_batch_poll that reports ready. */
 int nnmg_batch_reset(nnmg_handle* h, int mode, int nslots, double rtol, int maxit, void* stream);
 int nnmg_batch_admit(nnmg_handle* h, int slot, const double* b, int b_on_host, void* stream);
-int nnmg_batch_step(nnmg_handle* h, void* stream);
+int nnmg_batch_step(nnmg_handle* h, int iterations, void* stream);
 int nnmg_batch_poll(nnmg_handle* h, int wait, int* ready, int* active, int* iters,
                     double* relres, int* status);
 int nnmg_batch_retire(nnmg_handle* h, int slot, double* x, int x_on_host, void* stream);

@@ -60,7 +60,7 @@ PROTOTYPES = {
     "nnmg_set_nested": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "nnmg_batch_reset": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p]),
     "nnmg_batch_admit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
-    "nnmg_batch_step": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nnmg_batch_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_batch_poll": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "nnmg_batch_retire": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),

@@ -1137,17 +1137,19 @@ int nnmg_batch_admit(nnmg_handle* h, int slot, const double* b, int b_on_host, v
   return NNMG_OK;
 }
 
-int nnmg_batch_step(nnmg_handle* h, void* stream) {
-  if (!h || h->batch_mode < 0) {
-    set_error("nnmg_batch_step: no batch started");
+int nnmg_batch_step(nnmg_handle* h, int iterations, void* stream) {
+  if (!h || h->batch_mode < 0 || iterations < 1) {
+    set_error("nnmg_batch_step: no batch started or iterations < 1");
     return NNMG_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int mode = h->batch_mode, nslots = h->batch_slots;
-  int rc = run_graph(h, {1, mode, nslots}, s, [&](cudaStream_t st) {
-    return enqueue_pcg_iter(h, mode, nslots, st);
-  });
-  if (rc) return rc;
+  for (int it = 0; it < iterations; ++it) {
+    int rc = run_graph(h, {1, mode, nslots}, s, [&](cudaStream_t st) {
+      return enqueue_pcg_iter(h, mode, nslots, st);
+    });
+    if (rc) return rc;
+  }
   NNMG_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   NNMG_CUDA(cudaEventRecord(h->batch_ev, s));
   h->batch_inflight = true;
@@ -1192,7 +1194,6 @@ int nnmg_batch_retire(nnmg_handle* h, int slot, double* x, int x_on_host, void* 
                               sizeof(double), (size_t)L.rows,
                               x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
   NNMG_CUDA(cudaMemsetAsync(&h->sc->active[slot], 0, sizeof(int), s));
-  if (x_on_host) NNMG_CUDA(cudaStreamSynchronize(s));
   return NNMG_OK;
 }
 

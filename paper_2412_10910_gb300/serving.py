@@ -54,7 +54,15 @@ class FamilySpec:
 
 
 class FamilyEngine:
-    def __init__(self, name, spec, nslots=16, mode=_abi.FP32_MG_FP64_CG, rtol=1e-8, maxit=200):
+    """One mesh family: cached hierarchy, own stream, 16-slot PCG.
+
+    Right-hand sides and solutions pass through pinned per-slot staging
+    buffers, so admission and retirement copies are asynchronous; the host
+    waits once per poll.  When nothing is queued for the family, a step runs
+    up to `iters_per_step` iterations before the next host round trip."""
+
+    def __init__(self, name, spec, nslots=16, mode=_abi.FP32_MG_FP64_CG, rtol=1e-8, maxit=200,
+                 iters_per_step=4):
         import torch
         self.name = name
         self.spec = spec
@@ -71,6 +79,9 @@ class FamilyEngine:
         self.queue = collections.deque()
         self.inflight = False
         self.last_used = time.perf_counter()
+        self.iters_per_step = iters_per_step
+        self.b_stage = torch.empty(nslots, self.rows, dtype=torch.float64, pin_memory=True)
+        self.x_stage = torch.empty(nslots, self.rows, dtype=torch.float64, pin_memory=True)
         self._chk(self.lib.nnmg_batch_reset(self.H.h, mode, nslots, rtol, maxit, self.sptr), "reset")
         self._active = np.zeros(nslots, dtype=np.int32)
         self._iters = np.zeros(nslots, dtype=np.int32)
@@ -103,13 +114,14 @@ class FamilyEngine:
             for j in range(req.nrhs):
                 slot = self.owner.index(None)
                 self.owner[slot] = (req, j)
-                col = np.ascontiguousarray(req.b[:, j])
-                self._chk(self.lib.nnmg_batch_admit(self.H.h, slot, col.ctypes.data, 1, self.sptr),
-                          "admit")
+                self.b_stage[slot].numpy()[:] = req.b[:, j]
+                self._chk(self.lib.nnmg_batch_admit(self.H.h, slot, self.b_stage[slot].data_ptr(), 1,
+                                                    self.sptr), "admit")
 
     def step(self):
         if any(o is not None for o in self.owner) and not self.inflight:
-            self._chk(self.lib.nnmg_batch_step(self.H.h, self.sptr), "step")
+            n = 1 if self.queue else self.iters_per_step
+            self._chk(self.lib.nnmg_batch_step(self.H.h, n, self.sptr), "step")
             self.inflight = True
             self.last_used = time.perf_counter()
 
@@ -126,14 +138,18 @@ class FamilyEngine:
             return None
         self.inflight = False
         done = []
+        retired = []
         for slot, o in enumerate(self.owner):
             if o is None or self._active[slot]:
                 continue
-            req, j = o
-            col = np.empty(self.rows)
-            self._chk(self.lib.nnmg_batch_retire(self.H.h, slot, col.ctypes.data, 1, self.sptr),
-                      "retire")
-            req.x[:, j] = col
+            self._chk(self.lib.nnmg_batch_retire(self.H.h, slot, self.x_stage[slot].data_ptr(), 1,
+                                                 self.sptr), "retire")
+            retired.append(slot)
+        if retired:
+            self.stream.synchronize()                 # the retire copies
+        for slot in retired:
+            req, j = self.owner[slot]
+            req.x[:, j] = self.x_stage[slot].numpy()
             req.iters[j] = int(self._iters[slot])
             req.relres[j] = float(self._rel[slot])
             req.status[j] = int(self._status[slot])

@@ -84,7 +84,7 @@ def test_bad_arguments(nn):
     assert lib.nnmg_apply_operator(H.h, 2, _abi.F64, X, X, 4, s) == _abi.INVALID_ARG   # aliasing
     assert lib.nnmg_prolongate(H.h, 0, _abi.F64, X, Y, 4, s) == _abi.INVALID_ARG       # no coarser
     assert lib.nnmg_pcg_solve(H.h, 7, X, Y, 4, 1e-8, 10, None, None, s) == _abi.INVALID_ARG
-    assert lib.nnmg_batch_step(H.h, s) == _abi.INVALID_ARG                            # no batch
+    assert lib.nnmg_batch_step(H.h, 1, s) == _abi.INVALID_ARG                            # no batch
     assert lib.nnmg_restrict_noalloc(H.h, 0, _abi.F64, X, Y, 4, s) == _abi.INVALID_ARG
     with pytest.raises(ValueError):
         H.apply(2, x[:-1], y[:-1])                                                    # wrong size
