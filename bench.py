@@ -34,12 +34,44 @@ WORKLOAD = ("3D Poisson unit cube, Q2, 4 non-nested jittered hex levels 6^3/13^3
             "(+-0.15h, seeds 1-4), f=1 + 7 N(0,1) RHS, Chebyshev(3)-Jacobi, FP64 direct coarse, "
             "FP32 V-cycle in FP64 PCG, rtol 1e-8")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 CUDA-core peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
+# FP64 CUDA-core peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz;
+# the FP64 pipe takes one FMA, MUL or ADD per slot: 152 x 2 x 2.07e9 op/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PIPE_TOPS = 152 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
-# fine-level operator on this workload (404.6 + 66.0 MB).
-OP64_TRAFFIC_BYTES = 470.7e6
+# fine-level operator kernel the autotuner picks on this workload, or None
+# while the kernel has changed since the counters were taken.
+OP64_TRAFFIC_BYTES = None
+
+
+def poisson3d_work(n):
+    """(flops, FP64 pipe ops) per cell and right-hand side of the 3D Poisson
+    operator with n = k + 1 points per direction, as the sweeps run them:
+    12 line sweeps (3 interpolations, 3 derivatives, their transposes; two of
+    the transposed derivatives accumulate) and 9 multiply-adds of the metric
+    per quadrature point.  For odd n the sweeps skip S's unit middle row and
+    Dg's zero middle diagonal entry (exact for symmetric point sets)."""
+    odd = n % 2
+    rows = n - odd                                   # S rows that are not the unit row
+    s_flops, s_ops = rows * (2 * n - 1), rows * n    # S and S^T lines (same count)
+    d_flops = n * (2 * n - 1) - 2 * odd               # Dg or Dg^T line
+    d_ops = n * n - odd
+    da_flops, da_ops = 2 * n * n - 2 * odd, n * n - odd   # Dg^T accumulating into a line
+    lines = n * n
+    flops = lines * (6 * s_flops + 4 * d_flops + 2 * da_flops) + 15 * n ** 3
+    ops = lines * (6 * s_ops + 4 * d_ops + 2 * da_ops) + 9 * n ** 3
+    return flops, ops
+
+
+def operator_kernel_name(choice, k, dtype):
+    if choice == -1:
+        return f"op_reg_kernel<3,{k},{dtype}> (register-resident)"
+    if choice == -2:
+        return f"op_reg2_kernel<3,{k}> (paired FP32 register-resident)"
+    if choice > 0:
+        return f"op3d_kernel<{k},{dtype},1> ({choice} units per block)"
+    return f"default rule for <3,{k},{dtype}>"
 
 
 def _peaks():
@@ -546,11 +578,13 @@ def main():
     e2e_s = max_over_ranks((time.perf_counter() - t0) / ke)
 
     # ---- roofline of the dominant kernel: the FP64 fine-level operator (ALU bound)
-    n1 = cfg["degree"] + 1
-    fma_cell_rhs = 12 * n1 ** 4 + 9 * n1 ** 3   # 12 line sweeps of n1^4 FMA + metric
-    flops = 2.0 * fma_cell_rhs * n_cells * nrhs
+    flops_cell, ops_cell = poisson3d_work(cfg["degree"] + 1)
+    flops = float(flops_cell) * n_cells * nrhs
     op64_ms = statistics.mean(top64)
     achieved = flops / (op64_ms / 1e3) / 1e12
+    pipe = ops_cell * n_cells * nrhs / (op64_ms / 1e3) / 1e12
+    from paper_2412_10910_gb300 import _abi
+    choice64 = H.operator_choice(top, _abi.F64, nrhs)
     peaks, peak_kind = _peaks()
 
     line = {
@@ -573,11 +607,16 @@ def main():
         "operator_gdofs": {"f32": n_nodes * nrhs / (statistics.mean(top32) / 1e3) / 1e9,
                            "f64": n_nodes * nrhs / (op64_ms / 1e3) / 1e9,
                            "f64_double_word": n_nodes * nrhs / (statistics.mean(topdw) / 1e3) / 1e9},
-        "roofline": {"kernel": "op3d_kernel<2,double,1> (FP64 fine-level operator, 8 RHS)",
+        "roofline": {"kernel": operator_kernel_name(choice64, cfg["degree"], "double")
+                     + ", FP64 fine-level operator, 8 RHS",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "flops_per_cell_rhs": flops_cell,
+                     # the FP64 pipe issues FMA, MUL and ADD at the same rate: the
+                     # fraction of its slots the kernel's operations fill
+                     "fp64_ops_per_cell_rhs": ops_cell, "fp64_pipe_tops": pipe,
+                     "fp64_pipe_frac": pipe / FP64_PIPE_TOPS,
                      # DRAM bytes read + written per launch, ncu capture of this kernel
-                     # (profiles/op3d_f64_q2_c2_fine_8rhs.md)
                      "traffic": OP64_TRAFFIC_BYTES,
                      "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
         "e2e": {"value": dofs * world / e2e_s, "unit": UNIT,

@@ -160,6 +160,16 @@ int nnmg_quadrature_points(const nnmg_handle* h, int level, double* xq);
  * cell [n_free_fine], xi [n_free_fine][dim] (clamped to [0,1]^d). */
 int nnmg_transfer_points(const nnmg_handle* h, int fine_level, int32_t* cell, double* xi);
 
+/* Which operator kernel serves level `level` in arithmetic `precision`
+ * (enum nnmg_precision) for nrhs columns, as chosen so far on this handle
+ * (no counterpart in the paper: an implementation detail exposed for
+ * profiling).  *choice: -1 register-resident kernel (one thread per cell and
+ * column), -2 its paired FP32 form (one thread per cell and two columns), U > 0
+ * shared-memory kernel with U (cell, column) units per block, 0 the default
+ * rule (not tuned yet, autotuning off, or first used inside a stream capture).
+ * INVALID_ARG for a null handle or pointer, a bad level, precision or nrhs. */
+int nnmg_operator_choice(const nnmg_handle* h, int level, int precision, int nrhs, int* choice);
+
 /* Lanczos estimate of lambda_max(D^-1 A_l) per level ([n_levels]; 0 on level 0). */
 int nnmg_eigen_estimates(const nnmg_handle* h, double* lam_max);
 

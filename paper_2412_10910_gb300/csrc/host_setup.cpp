@@ -104,6 +104,9 @@ static void make_basis_uncached(int k, Basis1D<double>* b64, Basis1D<float>* b32
   double gl[kMaxN] = {0}, gx[kMaxN] = {0}, gw[kMaxN] = {0};
   gauss_lobatto(k, gl);
   gauss_legendre(n, gx, gw);
+  // For odd n both point sets contain the centre 1/2; store it exactly, so
+  // that S's middle row is exactly the unit row (the sweeps skip it).
+  if (n % 2 == 1) gl[n / 2] = gx[n / 2] = 0.5;
   Basis1D<double> b;
   std::memset(&b, 0, sizeof(b));
   for (int q = 0; q < n; ++q) {
@@ -112,6 +115,12 @@ static void make_basis_uncached(int k, Basis1D<double>* b64, Basis1D<float>* b32
       b.DS[q][l] = lagrange_der(gl, n, l, gx[q]);
       b.Dg[q][l] = lagrange_der(gx, n, l, gx[q]);
     }
+  }
+  if (n % 2 == 1) {
+    // the central Lagrange polynomial of a symmetric point set is even about
+    // 1/2: its derivative there vanishes exactly
+    b.Dg[n / 2][n / 2] = 0.0;
+    b.DS[n / 2][n / 2] = 0.0;
   }
   for (int l = 0; l < n; ++l) {
     b.gl[l] = gl[l];

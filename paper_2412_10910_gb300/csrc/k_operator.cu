@@ -40,24 +40,89 @@ __device__ __forceinline__ void add_out(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void add_out(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void add_out(double* p, dw v) { atomicAdd(p, dw_to_double(v)); }
 
-template <int N, typename T>
+// Two right-hand sides of one cell packed in a float pair: every operation is
+// one Blackwell packed FP32 instruction (add, multiply, fused multiply-add on
+// both halves, each rounded as its scalar FP32 counterpart).
+struct f2 {
+  float2 v;
+  __host__ __device__ f2() : v(make_float2(0.f, 0.f)) {}
+  __host__ __device__ f2(float a) : v(make_float2(a, a)) {}
+  __host__ __device__ f2(float2 a) : v(a) {}
+};
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+
+// s + m u: one FMA for float and double (contracted), one packed FMA for f2,
+// the double-word product and sum for dw.
+template <typename T>
+__device__ __forceinline__ T mac(T s, T m, T u) {
+  return s + m * u;
+}
+__device__ __forceinline__ f2 mac(f2 s, f2 m, f2 u) { return f2(__ffma2_rn(m.v, u.v, s.v)); }
+
+// The two 1D matrices of the sweeps: S interpolates from the Lobatto nodes to
+// the Gauss points, Dg differentiates by collocation on the Gauss points.  For
+// odd N the middle Gauss point is the middle Lobatto node (both are 1/2), so
+// S's middle row is the unit row and Dg's middle diagonal entry is zero (the
+// derivative there of the Lagrange polynomial of a symmetric point set at its
+// own, central node).  The host stores these entries exactly; the sweeps skip
+// them, which removes N of the N^2 products of every S sweep and one of every
+// Dg sweep.  A chain of products starts with its first product, so no type
+// (the double-word one in particular) pays for an addition of zero.
+enum { kInterp = 0, kDeriv = 1 };
+
+template <int N, int KIND>
+__host__ __device__ constexpr bool unit_row(int q) {
+  return KIND == kInterp && N % 2 == 1 && q == N / 2;
+}
+template <int N, int KIND>
+__host__ __device__ constexpr bool zero_entry(int q, int l) {
+  return N % 2 == 1 && (KIND == kInterp ? (q == N / 2 && l != N / 2)
+                                        : (q == N / 2 && l == N / 2));
+}
+
+// out = M in
+template <int N, int KIND, typename T>
 __device__ __forceinline__ void apply(const T (&M)[kMaxN][kMaxN], const T* in, T* out) {
 #pragma unroll
   for (int q = 0; q < N; ++q) {
-    T s = 0;
+    if (unit_row<N, KIND>(q)) {
+      out[q] = in[q];
+      continue;
+    }
+    T s;
+    bool first = true;
 #pragma unroll
-    for (int l = 0; l < N; ++l) s += M[q][l] * in[l];
+    for (int l = 0; l < N; ++l) {
+      if (zero_entry<N, KIND>(q, l)) continue;
+      s = first ? M[q][l] * in[l] : mac(s, M[q][l], in[l]);
+      first = false;
+    }
     out[q] = s;
   }
 }
 
-template <int N, typename T>
+// out = M^T in (add = false) or out += M^T in (add = true)
+template <int N, int KIND, bool ADD = false, typename T>
 __device__ __forceinline__ void apply_t(const T (&M)[kMaxN][kMaxN], const T* in, T* out) {
 #pragma unroll
   for (int l = 0; l < N; ++l) {
-    T s = 0;
+    T s;
+    bool first = true;
+    if (ADD) {
+      s = out[l];
+      first = false;
+    }
+    if (unit_row<N, KIND>(l)) {   // the unit entry M[l][l] = 1
+      s = first ? in[l] : s + in[l];
+      first = false;
+    }
 #pragma unroll
-    for (int q = 0; q < N; ++q) s += M[q][l] * in[q];
+    for (int q = 0; q < N; ++q) {
+      if (zero_entry<N, KIND>(q, l) || unit_row<N, KIND>(q)) continue;
+      s = first ? M[q][l] * in[q] : mac(s, M[q][l], in[q]);
+      first = false;
+    }
     out[l] = s;
   }
 }
@@ -124,7 +189,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
 #pragma unroll
     for (int l = 0; l < N; ++l)
       u[l] = dof[l] >= 0 ? to_arith(x[(int64_t)dof[l] * rs + c * nrhs + rhs], T()) : T(0);
-    apply<N>(B.S, u, v);
+    apply<N, kInterp>(B.S, u, v);
 #pragma unroll
     for (int q = 0; q < N; ++q) S(3 * c, a + N * b + N2 * q) = v[q];
   }
@@ -135,7 +200,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     T u[N], v[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) u[j] = S(3 * c, a + N * j + N2 * b);
-    apply<N>(B.S, u, v);
+    apply<N, kInterp>(B.S, u, v);
 #pragma unroll
     for (int q = 0; q < N; ++q) S(3 * c, a + N * q + N2 * b) = v[q];
   }
@@ -146,8 +211,8 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     T u[N], v[N], g[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) u[i] = S(3 * c, i + N * a + N2 * b);
-    apply<N>(B.S, u, v);
-    apply<N>(B.Dg, v, g);
+    apply<N, kInterp>(B.S, u, v);
+    apply<N, kDeriv>(B.Dg, v, g);
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       S(3 * c, q + N * a + N2 * b) = v[q];
@@ -161,7 +226,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     T u[N], g[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) u[p] = S(3 * c, a + N * p + N2 * b);
-    apply<N>(B.Dg, u, g);
+    apply<N, kDeriv>(B.Dg, u, g);
 #pragma unroll
     for (int q = 0; q < N; ++q) S(3 * c + 2, a + N * q + N2 * b) = g[q];
   }
@@ -175,7 +240,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
       T u[N];
 #pragma unroll
       for (int p = 0; p < N; ++p) u[p] = S(3 * c, a + N * b + N2 * p);
-      apply<N>(B.Dg, u, gz[c]);
+      apply<N, kDeriv>(B.Dg, u, gz[c]);
     }
 #pragma unroll
     for (int q = 0; q < N; ++q) {
@@ -210,7 +275,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       T w[N];
-      apply_t<N>(B.Dg, gz[c], w);
+      apply_t<N, kDeriv>(B.Dg, gz[c], w);
 #pragma unroll
       for (int p = 0; p < N; ++p) S(3 * c, a + N * b + N2 * p) = w[p];
     }
@@ -221,10 +286,13 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
   for (int c = 0; c < NC; ++c) {
     T f[N], w[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) f[q] = S(3 * c + 2, a + N * q + N2 * b);
-    apply_t<N>(B.Dg, f, w);
+    for (int q = 0; q < N; ++q) {
+      f[q] = S(3 * c + 2, a + N * q + N2 * b);
+      w[q] = S(3 * c, a + N * q + N2 * b);
+    }
+    apply_t<N, kDeriv, true>(B.Dg, f, w);
 #pragma unroll
-    for (int p = 0; p < N; ++p) S(3 * c, a + N * p + N2 * b) += w[p];
+    for (int p = 0; p < N; ++p) S(3 * c, a + N * p + N2 * b) = w[p];
   }
   __syncthreads();
   // P7: add the transposed x derivative and integrate along x, line (y=a, z=b)
@@ -232,11 +300,12 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
   for (int c = 0; c < NC; ++c) {
     T f[N], w[N], o[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) f[q] = S(3 * c + 1, q + N * a + N2 * b);
-    apply_t<N>(B.Dg, f, w);
-#pragma unroll
-    for (int q = 0; q < N; ++q) w[q] += S(3 * c, q + N * a + N2 * b);
-    apply_t<N>(B.S, w, o);
+    for (int q = 0; q < N; ++q) {
+      f[q] = S(3 * c + 1, q + N * a + N2 * b);
+      w[q] = S(3 * c, q + N * a + N2 * b);
+    }
+    apply_t<N, kDeriv, true>(B.Dg, f, w);
+    apply_t<N, kInterp>(B.S, w, o);
 #pragma unroll
     for (int i = 0; i < N; ++i) S(3 * c, i + N * a + N2 * b) = o[i];
   }
@@ -247,7 +316,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     T f[N], o[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) f[q] = S(3 * c, a + N * q + N2 * b);
-    apply_t<N>(B.S, f, o);
+    apply_t<N, kInterp>(B.S, f, o);
 #pragma unroll
     for (int j = 0; j < N; ++j) S(3 * c, a + N * j + N2 * b) = o[j];
   }
@@ -258,7 +327,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     T f[N], o[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) f[q] = S(3 * c, a + N * b + N2 * q);
-    apply_t<N>(B.S, f, o);
+    apply_t<N, kInterp>(B.S, f, o);
 #pragma unroll
     for (int l = 0; l < N; ++l)
       if (dof[l] >= 0) add_out(&y[(int64_t)dof[l] * rs + c * nrhs + rhs], o[l]);
@@ -288,7 +357,7 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
       dof[j] = act ? cell_nodes[cell * NQ + a + N * j] : -1;
       u[j] = dof[j] >= 0 ? to_arith(x[(int64_t)dof[j] * nrhs + rhs], T()) : T(0);
     }
-    apply<N>(B.S, u, v);
+    apply<N, kInterp>(B.S, u, v);
 #pragma unroll
     for (int q = 0; q < N; ++q) S(0, a + N * q) = v[q];
   }
@@ -297,8 +366,8 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     T u[N], v[N], g[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) u[i] = S(0, i + N * a);
-    apply<N>(B.S, u, v);
-    apply<N>(B.Dg, v, g);
+    apply<N, kInterp>(B.S, u, v);
+    apply<N, kDeriv>(B.Dg, v, g);
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       S(0, q + N * a) = v[q];
@@ -310,7 +379,7 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     T u[N], gy[N], w[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) u[p] = S(0, a + N * p);
-    apply<N>(B.Dg, u, gy);
+    apply<N, kDeriv>(B.Dg, u, gy);
     const T* mc = metric + (act ? cell : 0) * 3 * NQ;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
@@ -321,7 +390,7 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
       S(1, idx) = G0 * gx + G1 * gy[q];
       gy[q] = G1 * gx + G2 * gy[q];
     }
-    apply_t<N>(B.Dg, gy, w);
+    apply_t<N, kDeriv>(B.Dg, gy, w);
 #pragma unroll
     for (int p = 0; p < N; ++p) S(0, a + N * p) = w[p];
   }
@@ -329,11 +398,12 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
   {  // transposed x derivative + x integration, row y = a
     T f[N], w[N], o[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) f[q] = S(1, q + N * a);
-    apply_t<N>(B.Dg, f, w);
-#pragma unroll
-    for (int q = 0; q < N; ++q) w[q] += S(0, q + N * a);
-    apply_t<N>(B.S, w, o);
+    for (int q = 0; q < N; ++q) {
+      f[q] = S(1, q + N * a);
+      w[q] = S(0, q + N * a);
+    }
+    apply_t<N, kDeriv, true>(B.Dg, f, w);
+    apply_t<N, kInterp>(B.S, w, o);
 #pragma unroll
     for (int i = 0; i < N; ++i) S(0, i + N * a) = o[i];
   }
@@ -342,7 +412,7 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
     T f[N], o[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) f[q] = S(0, a + N * q);
-    apply_t<N>(B.S, f, o);
+    apply_t<N, kInterp>(B.S, f, o);
 #pragma unroll
     for (int j = 0; j < N; ++j)
       if (dof[j] >= 0) add_out(&y[(int64_t)dof[j] * nrhs + rhs], o[j]);
@@ -355,10 +425,13 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
 // reference gradients and the fluxes in registers, so the sweeps need no
 // shared memory and no barriers.  Consecutive threads are consecutive units
 // (right-hand side fastest), so a warp's gathers of one local node cover
-// whole 32-byte rows of right-hand sides.
-template <int D, int N, typename T>
-__device__ __forceinline__ void sweep(const T (&M)[kMaxN][kMaxN], T* v, int dir, bool transpose) {
-  // apply M (or M^T) along direction dir to every line of the N^D array v
+// whole 32-byte rows of right-hand sides.  In FP64 (and double-word) the
+// 1/64-rate FP64 pipe bounds the kernel and the barrier-free schedule keeps
+// it busy; 253 registers a thread still fit two 128-thread blocks per SM.
+template <int D, int N, int KIND, bool TRANSPOSE, bool ADD = false, typename T>
+__device__ __forceinline__ void sweep(const T (&M)[kMaxN][kMaxN], const T* f, T* v, int dir) {
+  // v = M (or M^T) applied along direction dir to every line of the N^D
+  // array f; with ADD the result is added to v instead (TRANSPOSE only)
   constexpr int NQ = D == 2 ? N * N : N * N * N;
   const int stride = dir == 0 ? 1 : (dir == 1 ? N : N * N);
 #pragma unroll
@@ -367,38 +440,24 @@ __device__ __forceinline__ void sweep(const T (&M)[kMaxN][kMaxN], T* v, int dir,
     if (coord != 0) continue;
     T in[N], out[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) in[i] = v[base + i * stride];
-    if (transpose)
-      apply_t<N>(M, in, out);
+    for (int i = 0; i < N; ++i) {
+      in[i] = f[base + i * stride];
+      if (ADD) out[i] = v[base + i * stride];
+    }
+    if constexpr (TRANSPOSE)
+      apply_t<N, KIND, ADD>(M, in, out);
     else
-      apply<N>(M, in, out);
+      apply<N, KIND>(M, in, out);
 #pragma unroll
     for (int i = 0; i < N; ++i) v[base + i * stride] = out[i];
-  }
-}
-
-template <int D, int N, typename T>
-__device__ __forceinline__ void sweep_add_t(const T (&M)[kMaxN][kMaxN], const T* f, T* w, int dir) {
-  // w += M^T applied along dir to f
-  constexpr int NQ = D == 2 ? N * N : N * N * N;
-  const int stride = dir == 0 ? 1 : (dir == 1 ? N : N * N);
-#pragma unroll
-  for (int base = 0; base < NQ; ++base) {
-    const int coord = (base / stride) % N;
-    if (coord != 0) continue;
-    T in[N], out[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) in[i] = f[base + i * stride];
-    apply_t<N>(M, in, out);
-#pragma unroll
-    for (int i = 0; i < N; ++i) w[base + i * stride] += out[i];
   }
 }
 
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__ cell_nodes,
                                                      const T* __restrict__ metric,
-                                                     const T* __restrict__ x, T* __restrict__ y,
+                                                     const typename io_of<T>::type* __restrict__ x,
+                                                     typename io_of<T>::type* __restrict__ y,
                                                      int64_t n_cells, int nrhs, Basis1D<T> B) {
   constexpr int N = K + 1;
   constexpr int NQ = D == 2 ? N * N : N * N * N;
@@ -412,19 +471,14 @@ __global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__
 #pragma unroll
   for (int i = 0; i < NQ; ++i) {
     const int dof = cn[i];
-    v[i] = dof >= 0 ? x[(int64_t)dof * nrhs + rhs] : T(0);
+    v[i] = dof >= 0 ? to_arith(x[(int64_t)dof * nrhs + rhs], T()) : T(0);
   }
   // values at the Gauss points, then collocation derivatives
 #pragma unroll
-  for (int d = 0; d < D; ++d) sweep<D, N, T>(B.S, v, d, false);
-#pragma unroll
-  for (int i = 0; i < NQ; ++i) {
-    gx[i] = v[i];
-    gy[i] = v[i];
-  }
-  sweep<D, N, T>(B.Dg, gx, 0, false);
-  sweep<D, N, T>(B.Dg, gy, 1, false);
-  if constexpr (D == 3) sweep<D, N, T>(B.Dg, v, 2, false);  // v now holds d/dz
+  for (int d = 0; d < D; ++d) sweep<D, N, kInterp, false>(B.S, v, v, d);
+  sweep<D, N, kDeriv, false>(B.Dg, v, gx, 0);
+  sweep<D, N, kDeriv, false>(B.Dg, v, gy, 1);
+  if constexpr (D == 3) sweep<D, N, kDeriv, false>(B.Dg, v, v, 2);  // v now holds d/dz
   // metric terms: flux = G grad^
   const T* mc = metric + cell * NM * NQ;
 #pragma unroll
@@ -445,21 +499,83 @@ __global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__
   }
   // w = Dx^T fx + Dy^T fy (+ Dz^T fz), then integrate with S^T
   if constexpr (D == 3) {
-    sweep<D, N, T>(B.Dg, v, 2, true);
-    sweep_add_t<D, N, T>(B.Dg, gy, v, 1);
-    sweep_add_t<D, N, T>(B.Dg, gx, v, 0);
+    sweep<D, N, kDeriv, true>(B.Dg, v, v, 2);
+    sweep<D, N, kDeriv, true, true>(B.Dg, gy, v, 1);
+    sweep<D, N, kDeriv, true, true>(B.Dg, gx, v, 0);
   } else {
-    sweep<D, N, T>(B.Dg, gy, 1, true);
-    sweep_add_t<D, N, T>(B.Dg, gx, gy, 0);
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) v[i] = gy[i];
+    sweep<D, N, kDeriv, true>(B.Dg, gy, v, 1);
+    sweep<D, N, kDeriv, true, true>(B.Dg, gx, v, 0);
   }
 #pragma unroll
-  for (int d = 0; d < D; ++d) sweep<D, N, T>(B.S, v, d, true);
+  for (int d = 0; d < D; ++d) sweep<D, N, kInterp, true>(B.S, v, v, d);
 #pragma unroll
   for (int i = 0; i < NQ; ++i) {
     const int dof = cn[i];
-    if (dof >= 0) atomicAdd(&y[(int64_t)dof * nrhs + rhs], v[i]);
+    if (dof >= 0) add_out(&y[(int64_t)dof * nrhs + rhs], v[i]);
+  }
+}
+
+// Paired FP32 variant (even number of right-hand sides): one thread per cell
+// and pair of right-hand sides, each value an f2.  Every FMA, index load,
+// metric load and atomic then serves two right-hand sides, which halves the
+// instruction count of this issue-bound kernel; vectors are read and written
+// as float pairs (8-byte aligned rows of right-hand sides).
+template <int D, int K>
+__global__ void __launch_bounds__(128) op_reg2_kernel(const int32_t* __restrict__ cell_nodes,
+                                                      const float* __restrict__ metric,
+                                                      const float2* __restrict__ x,
+                                                      float2* __restrict__ y, int64_t n_cells,
+                                                      int npair, Basis1D<f2> B) {
+  constexpr int N = K + 1;
+  constexpr int NQ = D == 2 ? N * N : N * N * N;
+  constexpr int NM = D == 2 ? 3 : 6;
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cell = u / npair;
+  if (cell >= n_cells) return;
+  const int pr = (int)(u - cell * npair);
+  const int32_t* cn = cell_nodes + cell * NQ;
+  f2 v[NQ], gx[NQ], gy[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int dof = cn[i];
+    v[i] = dof >= 0 ? f2(x[(int64_t)dof * npair + pr]) : f2();
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) sweep<D, N, kInterp, false>(B.S, v, v, d);
+  sweep<D, N, kDeriv, false>(B.Dg, v, gx, 0);
+  sweep<D, N, kDeriv, false>(B.Dg, v, gy, 1);
+  if constexpr (D == 3) sweep<D, N, kDeriv, false>(B.Dg, v, v, 2);
+  const float* mc = metric + cell * NM * NQ;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if constexpr (D == 3) {
+      const f2 a = gx[q], b = gy[q], c = v[q];
+      const f2 G0(mc[q]), G1(mc[NQ + q]), G2(mc[2 * NQ + q]), G3(mc[3 * NQ + q]),
+          G4(mc[4 * NQ + q]), G5(mc[5 * NQ + q]);
+      gx[q] = mac(mac(G0 * a, G1, b), G2, c);
+      gy[q] = mac(mac(G1 * a, G3, b), G4, c);
+      v[q] = mac(mac(G2 * a, G4, b), G5, c);
+    } else {
+      const f2 a = gx[q], b = gy[q];
+      const f2 G0(mc[q]), G1(mc[NQ + q]), G2(mc[2 * NQ + q]);
+      gx[q] = mac(G0 * a, G1, b);
+      gy[q] = mac(G1 * a, G2, b);
+    }
+  }
+  if constexpr (D == 3) {
+    sweep<D, N, kDeriv, true>(B.Dg, v, v, 2);
+    sweep<D, N, kDeriv, true, true>(B.Dg, gy, v, 1);
+    sweep<D, N, kDeriv, true, true>(B.Dg, gx, v, 0);
+  } else {
+    sweep<D, N, kDeriv, true>(B.Dg, gy, v, 1);
+    sweep<D, N, kDeriv, true, true>(B.Dg, gx, v, 0);
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) sweep<D, N, kInterp, true>(B.S, v, v, d);
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int dof = cn[i];
+    if (dof >= 0) atomicAdd(&y[(int64_t)dof * npair + pr], v[i].v);
   }
 }
 
@@ -490,6 +606,24 @@ void pick_basis<dw>(int k, Basis1D<dw>* b) {
     b->gl_scale[i] = dw_split_host(d.gl_scale[i]);
     b->gx[i] = dw_split_host(d.gx[i]);
     b->gw[i] = dw_split_host(d.gw[i]);
+  }
+}
+
+template <>
+void pick_basis<f2>(int k, Basis1D<f2>* b) {
+  Basis1D<double> d;
+  Basis1D<float> f;
+  make_basis(k, &d, &f);
+  for (int i = 0; i < kMaxN; ++i) {
+    for (int j = 0; j < kMaxN; ++j) {
+      b->S[i][j] = f2(f.S[i][j]);
+      b->Dg[i][j] = f2(f.Dg[i][j]);
+      b->DS[i][j] = f2(f.DS[i][j]);
+    }
+    b->gl[i] = f2(f.gl[i]);
+    b->gl_scale[i] = f2(f.gl_scale[i]);
+    b->gx[i] = f2(f.gx[i]);
+    b->gw[i] = f2(f.gw[i]);
   }
 }
 
@@ -600,8 +734,8 @@ const dw* metric_of<dw>(const DevLevel& L) { return reinterpret_cast<const dw*>(
 }  // namespace
 
 template <int D, int K, typename T>
-cudaError_t run_reg(const DevLevel& L, const T* metric, const T* x, T* y, int nrhs,
-                    cudaStream_t s) {
+cudaError_t run_reg(const DevLevel& L, const T* metric, const typename io_of<T>::type* x,
+                    typename io_of<T>::type* y, int nrhs, cudaStream_t s) {
   Basis1D<T> B;
   pick_basis<T>(K, &B);
   const int64_t units = L.n_cells * nrhs;
@@ -610,12 +744,28 @@ cudaError_t run_reg(const DevLevel& L, const T* metric, const T* x, T* y, int nr
   return cudaGetLastError();
 }
 
-// The register-resident kernel serves FP32 Poisson cells with at most 27
-// (3D) or 25 (2D) nodes; units < 0 asks for it explicitly, units > 0 for the
-// shared-memory kernel with that many units per block (autotuner choices).
+template <int D, int K>
+cudaError_t run_reg2(const DevLevel& L, const float* metric, const float* x, float* y, int nrhs,
+                     cudaStream_t s) {
+  Basis1D<f2> B;
+  pick_basis<f2>(K, &B);
+  const int npair = nrhs / 2;
+  const int64_t units = L.n_cells * npair;
+  op_reg2_kernel<D, K><<<(unsigned)((units + 127) / 128), 128, 0, s>>>(
+      L.cell_nodes, metric, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y),
+      L.n_cells, npair, B);
+  return cudaGetLastError();
+}
+
+// The register-resident kernel serves Poisson cells with at most 27 (3D) or
+// 25 (2D) nodes, in every arithmetic type; units < 0 asks for it explicitly,
+// units = -2 for its paired FP32 form (even
+// nrhs, 8-byte aligned vectors; otherwise the unpaired one runs), units > 0
+// for the shared-memory kernel with that many units per block (autotuner
+// choices), units = 0 for the default (the register kernel where it applies).
 template <typename T>
 bool reg_eligible(const DevLevel& L) {
-  return sizeof(T) == 4 && L.ncomp == 1 && (L.dim == 2 || L.k <= 2);
+  return L.ncomp == 1 && (L.dim == 2 || L.k <= 2);
 }
 
 template <typename T>
@@ -626,11 +776,17 @@ cudaError_t launch_operator_impl(const DevLevel& L, const typename io_of<T>::typ
   const T* m = metric_of<T>(L);
   if (!m) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
-    if (reg_eligible<T>(L) && units <= 0) {
-#define NNMG_REG(D, K) if (L.dim == D && L.k == K) return run_reg<D, K, T>(L, m, x, y, nrhs, s);
-      NNMG_REG(2, 1) NNMG_REG(2, 2) NNMG_REG(2, 3) NNMG_REG(2, 4) NNMG_REG(3, 1) NNMG_REG(3, 2)
-#undef NNMG_REG
+    if (reg_eligible<T>(L) && units == -2 && nrhs % 2 == 0 && (uintptr_t)x % 8 == 0 &&
+        (uintptr_t)y % 8 == 0) {
+#define NNMG_REG2(D, K) if (L.dim == D && L.k == K) return run_reg2<D, K>(L, m, x, y, nrhs, s);
+      NNMG_REG2(2, 1) NNMG_REG2(2, 2) NNMG_REG2(2, 3) NNMG_REG2(2, 4) NNMG_REG2(3, 1) NNMG_REG2(3, 2)
+#undef NNMG_REG2
     }
+  }
+  if (reg_eligible<T>(L) && units <= 0) {
+#define NNMG_REG(D, K) if (L.dim == D && L.k == K) return run_reg<D, K, T>(L, m, x, y, nrhs, s);
+    NNMG_REG(2, 1) NNMG_REG(2, 2) NNMG_REG(2, 3) NNMG_REG(2, 4) NNMG_REG(3, 1) NNMG_REG(3, 2)
+#undef NNMG_REG
   }
   if (L.dim == 2) {
     switch (L.k) {
@@ -685,6 +841,7 @@ int operator_unit_candidates(const DevLevel& L, int nrhs, int* out, int max_out)
   if (lines == 0) return 0;
   int n = 0;
   if (reg_eligible<T>(L) && max_out > 0) out[n++] = -1;   // the register-resident kernel
+  if (sizeof(T) == 4 && reg_eligible<T>(L) && nrhs % 2 == 0 && n < max_out) out[n++] = -2;
   return n + unit_candidates(lines, nrhs, mt, per_unit, out + n, max_out - n);
 }
 

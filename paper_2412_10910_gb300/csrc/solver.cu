@@ -10,6 +10,7 @@
 #include <map>
 #include <new>
 #include <tuple>
+#include <type_traits>
 
 #include "nnmg_internal.h"
 
@@ -150,17 +151,25 @@ int ensure_pcg(nnmg_handle* h) {
 }
 
 // ------------------------------------------------------------------ autotuner
-// Units per block of the operator kernel for (level, precision, nrhs): on first
-// use every legal choice is timed (one warm-up and three timed launches on
-// scratch vectors, CUDA events) and the fastest is kept for the handle's
-// lifetime.  Never runs during stream capture (the default rule is used then)
-// and is skipped when the environment sets NNMG_AUTOTUNE=0.
-template <typename T>
-int op_units(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
-  const int prec = sizeof(T) == 8 ? NNMG_F64 : NNMG_F32;
-  auto key = std::make_tuple(level, prec, nrhs);
+// Operator kernel choice for (level, precision, nrhs): -1 the register-resident
+// kernel, -2 its paired FP32 form, U > 0 the shared-memory kernel with U units
+// per block, 0 the default rule.  On first use every legal choice is timed
+// (one warm-up and three timed launches on scratch vectors, CUDA events) and
+// the fastest is kept for the handle's lifetime.  Never runs during stream
+// capture (the default rule is used then); NNMG_AUTOTUNE=0 in the
+// environment keeps the default rule, NNMG_OP_CHOICE=<c> forces choice c on
+// every level (a choice that does not apply to a level falls back to the
+// default there).
+template <typename T, typename Launch>
+int tune_units(nnmg_handle* h, int level, int prec_key, int nrhs, cudaStream_t s, Launch launch) {
+  auto key = std::make_tuple(level, prec_key, nrhs);
   auto it = h->op_units.find(key);
   if (it != h->op_units.end()) return it->second;
+  if (const char* f = getenv("NNMG_OP_CHOICE")) {
+    const int c = atoi(f);
+    h->op_units[key] = c;
+    return c;
+  }
   static const bool enabled = [] {
     const char* e = getenv("NNMG_AUTOTUNE");
     return !(e && e[0] == '0');
@@ -173,18 +182,18 @@ int op_units(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
   const int nc = operator_unit_candidates<T>(L, nrhs, cand, 8);
   int best = 0;
   if (nc > 1 && L.n_cells > 0) {
-    T *x = nullptr, *y = nullptr;
+    using IO = std::conditional_t<sizeof(T) == 4, float, double>;
+    IO *x = nullptr, *y = nullptr;
     const size_t n = (size_t)L.rows * nrhs;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaMalloc(&x, n * sizeof(T)) == cudaSuccess && cudaMalloc(&y, n * sizeof(T)) == cudaSuccess &&
-        cudaMemsetAsync(x, 0, n * sizeof(T), s) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+    if (cudaMalloc(&x, n * sizeof(IO)) == cudaSuccess && cudaMalloc(&y, n * sizeof(IO)) == cudaSuccess &&
+        cudaMemsetAsync(x, 0, n * sizeof(IO), s) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
         cudaEventCreate(&e1) == cudaSuccess) {
       float best_ms = 1e30f;
       for (int c = 0; c < nc; ++c) {
-        bool ok = launch_operator<T>(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, cand[c]) == cudaSuccess;
+        bool ok = launch(L, x, y, cand[c]) == cudaSuccess;
         ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
-        for (int r = 0; r < 3 && ok; ++r)
-          ok = launch_operator<T>(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, cand[c]) == cudaSuccess;
+        for (int r = 0; r < 3 && ok; ++r) ok = launch(L, x, y, cand[c]) == cudaSuccess;
         ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
         float ms = 0.f;
         if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
@@ -203,53 +212,20 @@ int op_units(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
   return best;
 }
 
-// Same as op_units for the double-word operator (FP64 vectors).
+template <typename T>
+int op_units(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
+  return tune_units<T>(h, level, sizeof(T) == 8 ? NNMG_F64 : NNMG_F32, nrhs, s,
+                       [&](const DevLevel& L, T* x, T* y, int c) {
+                         return launch_operator<T>(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, c);
+                       });
+}
+
+// The double-word operator (FP64 vectors, FP32 pipes).
 int op_units_dw(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
-  auto key = std::make_tuple(level, (int)NNMG_F64_DW, nrhs);
-  auto it = h->op_units.find(key);
-  if (it != h->op_units.end()) return it->second;
-  static const bool enabled = [] {
-    const char* e = getenv("NNMG_AUTOTUNE");
-    return !(e && e[0] == '0');
-  }();
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (!enabled || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
-    return 0;
-  const DevLevel& L = h->lv[level];
-  int cand[8];
-  const int nc = operator_unit_candidates<double>(L, nrhs, cand, 8);
-  int best = 0;
-  if (nc > 1 && L.n_cells > 0) {
-    double *x = nullptr, *y = nullptr;
-    const size_t n = (size_t)L.rows * nrhs;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaMalloc(&x, n * sizeof(double)) == cudaSuccess &&
-        cudaMalloc(&y, n * sizeof(double)) == cudaSuccess &&
-        cudaMemsetAsync(x, 0, n * sizeof(double), s) == cudaSuccess &&
-        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
-      float best_ms = 1e30f;
-      for (int c = 0; c < nc; ++c) {
-        if (cand[c] <= 0) continue;
-        bool ok = launch_operator_dw(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, cand[c]) == cudaSuccess;
-        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
-        for (int r = 0; r < 3 && ok; ++r)
-          ok = launch_operator_dw(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, cand[c]) == cudaSuccess;
-        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
-        float ms = 0.f;
-        if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
-          best_ms = ms;
-          best = cand[c];
-        }
-      }
-    }
-    cudaGetLastError();
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (x) cudaFree(x);
-    if (y) cudaFree(y);
-  }
-  h->op_units[key] = best;
-  return best;
+  return tune_units<double>(h, level, NNMG_F64_DW, nrhs, s,
+                            [&](const DevLevel& L, double* x, double* y, int c) {
+                              return launch_operator_dw(L, x, y, nrhs, h->opt.lambda, h->opt.mu, s, c);
+                            });
 }
 
 // ------------------------------------------------------------------ V-cycle
@@ -915,6 +891,17 @@ int nnmg_transfer_points(const nnmg_handle* h, int fine_level, int32_t* cell, do
   const DevLevel& F = h->lv[fine_level];
   if (cell) std::memcpy(cell, F.h_loc_cell.data(), F.h_loc_cell.size() * sizeof(int32_t));
   if (xi) std::memcpy(xi, F.h_loc_xi.data(), F.h_loc_xi.size() * sizeof(double));
+  return NNMG_OK;
+}
+
+int nnmg_operator_choice(const nnmg_handle* h, int level, int precision, int nrhs, int* choice) {
+  if (!h || !choice || level < 0 || level >= (int)h->lv.size() || nrhs < 1 ||
+      nrhs > kMaxRhs || (precision != NNMG_F32 && precision != NNMG_F64 && precision != NNMG_F64_DW)) {
+    set_error("nnmg_operator_choice: bad handle, pointer, level, precision or nrhs");
+    return NNMG_INVALID_ARG;
+  }
+  auto it = h->op_units.find(std::make_tuple(level, precision, nrhs));
+  *choice = it == h->op_units.end() ? 0 : it->second;
   return NNMG_OK;
 }
 

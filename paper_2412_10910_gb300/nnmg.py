@@ -151,6 +151,12 @@ def nnmg_transfer_points(h, fine_level, dim):
     return cell, xi
 
 
+def nnmg_operator_choice(h, level, precision, nrhs):
+    out = C.c_int(0)
+    _check(_lib.nnmg_operator_choice(h, level, precision, nrhs, C.byref(out)), "nnmg_operator_choice")
+    return out.value
+
+
 def nnmg_eigen_estimates(h):
     out = np.empty(nnmg_n_levels(h))
     _check(_lib.nnmg_eigen_estimates(h, out.ctypes.data), "nnmg_eigen_estimates")
@@ -330,6 +336,11 @@ class Hierarchy:
 
     def eigen_estimates(self):
         return nnmg_eigen_estimates(self.h)
+
+    def operator_choice(self, level, precision, nrhs):
+        """-1 register kernel, -2 paired FP32 register kernel, U > 0 shared-memory
+        kernel with U units per block, 0 default rule / not chosen yet."""
+        return nnmg_operator_choice(self.h, level, precision, nrhs)
 
     def load_vector(self, level, f, b, col=0, per_qp=False):
         nnmg_load_vector(self.h, level, f, per_qp, b, self._nrhs(b), col, ncomp=self.ncomp)
