@@ -40,9 +40,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_PIPE_TOPS = 152 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
-# fine-level operator kernel the autotuner picks on this workload, or None
-# while the kernel has changed since the counters were taken.
-OP64_TRAFFIC_BYTES = None
+# fine-level operator on this workload, for the kernel choice the counters
+# were taken on (404.5 + 65.5 MB, op_reg_kernel<3,2,double>); reported only
+# when the autotuner picks that kernel.
+OP64_TRAFFIC = {-1: 470.0e6}
 
 
 def poisson3d_work(n):
@@ -270,6 +271,7 @@ def run_configs(args, rank):
                "levels": [list(lv.n) for lv in levels], "level_degrees": degs, "fine_free_dofs":
                int(nfree) * cfg["ncomp"], "nrhs": nrhs, "setup_s": setup_s,
                "setup_dofs_per_s": int(nn) * cfg["ncomp"] / setup_s,
+               "setup_phases_s": H.setup_seconds(),
                "hierarchy_bytes": H.hierarchy_bytes()}
         for mode, tag in [(_abi.FP32_MG_FP64_CG, "fp32_mg_fp64_cg"), (_abi.FP64_MG, "fp64_mg"),
                           (_abi.FP32_MG_DW_CG, "fp32_mg_dw_cg")]:
@@ -607,18 +609,19 @@ def main():
         "operator_gdofs": {"f32": n_nodes * nrhs / (statistics.mean(top32) / 1e3) / 1e9,
                            "f64": n_nodes * nrhs / (op64_ms / 1e3) / 1e9,
                            "f64_double_word": n_nodes * nrhs / (statistics.mean(topdw) / 1e3) / 1e9},
+        # The FP64 pipe takes one FMA, MUL or ADD per slot, 2 per clock per SM:
+        # the roofline counts the kernel's FP64 operations against those slots
+        # (flops beside it: an ADD is one flop in a full slot).
         "roofline": {"kernel": operator_kernel_name(choice64, cfg["degree"], "double")
                      + ", FP64 fine-level operator, 8 RHS",
-                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "flops_per_cell_rhs": flops_cell,
-                     # the FP64 pipe issues FMA, MUL and ADD at the same rate: the
-                     # fraction of its slots the kernel's operations fill
-                     "fp64_ops_per_cell_rhs": ops_cell, "fp64_pipe_tops": pipe,
-                     "fp64_pipe_frac": pipe / FP64_PIPE_TOPS,
+                     "bound": "alu", "achieved": pipe, "peak": FP64_PIPE_TOPS,
+                     "unit": "T FP64-pipe op/s (FMA, MUL or ADD)", "frac": pipe / FP64_PIPE_TOPS,
+                     "ops_per_cell_rhs": ops_cell, "flops_per_cell_rhs": flops_cell,
+                     "achieved_tflops": achieved, "peak_tflops": FP64_PEAK_TFLOPS,
                      # DRAM bytes read + written per launch, ncu capture of this kernel
-                     "traffic": OP64_TRAFFIC_BYTES,
-                     "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
+                     "traffic": OP64_TRAFFIC.get(choice64),
+                     "peak_source": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz "
+                                    "(an FMA-chain probe reached 0.596 T/s = 0.95 of it)"},
         "e2e": {"value": dofs * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": rows * nrhs * 8, "d2h_bytes_per_step": rows * nrhs * 8},
         "gpu_launches": kernels_per_solve(H.n_levels, cfg["cheb"], int(max(iters))) * args.steps,

@@ -55,7 +55,8 @@ typedef struct nnmg_handle nnmg_handle;
 enum nnmg_status {
   NNMG_OK = 0,
   NNMG_INVALID_ARG = 1,     /* bad pointer, size, level index, nrhs or option   */
-  NNMG_BAD_MESH = 2,        /* non-positive Jacobian determinant at a quadrature point */
+  NNMG_BAD_MESH = 2,        /* non-positive Jacobian determinant at a quadrature point, or a
+                               non-conforming mesh (a shared face with inconsistent vertex order) */
   NNMG_POINT_NOT_FOUND = 3, /* a fine support point could not be located         */
   NNMG_CHOLESKY_FAIL = 4,   /* coarsest matrix not positive definite             */
   NNMG_OUT_OF_MEMORY = 5,   /* device or host allocation failed                  */
@@ -159,6 +160,16 @@ int nnmg_quadrature_points(const nnmg_handle* h, int level, double* xq);
  * level fine_level >= 1 (Sec. 3.1), in increasing fine node order:
  * cell [n_free_fine], xi [n_free_fine][dim] (clamped to [0,1]^d). */
 int nnmg_transfer_points(const nnmg_handle* h, int fine_level, int32_t* cell, double* xi);
+
+/* Wall seconds of the setup phases of this hierarchy (no counterpart in the
+ * paper, which does not time setup): seconds[NNMG_SETUP_PHASES] =
+ * {0 node numbering (host), 1 per-level device geometry: metric terms,
+ * support points, diagonal, 2 point location and transfer lists,
+ * 3 restriction gather lists (host), 4 Lanczos eigenvalue estimates,
+ * 5 coarsest operator assembly and dense inverse}.  INVALID_ARG for a null
+ * handle or pointer. */
+#define NNMG_SETUP_PHASES 6
+int nnmg_setup_seconds(const nnmg_handle* h, double* seconds);
 
 /* Which operator kernel serves level `level` in arithmetic `precision`
  * (enum nnmg_precision) for nrhs columns, as chosen so far on this handle

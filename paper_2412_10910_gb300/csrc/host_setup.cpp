@@ -4,7 +4,6 @@
 #include <algorithm>
 #include <cmath>
 #include <thread>
-#include <unordered_map>
 
 #include "nnmg_internal.h"
 
@@ -147,113 +146,192 @@ static void make_basis_uncached(int k, Basis1D<double>* b64, Basis1D<float>* b32
 
 // ------------------------------------------------------------ numbering
 namespace {
-struct Key {
-  int32_t v[4];
-  int32_t w[4];
-  int n;
-  bool operator==(const Key& o) const {
-    if (n != o.n) return false;
-    for (int i = 0; i < n; ++i)
-      if (v[i] != o.v[i] || w[i] != o.w[i]) return false;
+// Mesh entities shared between cells: edges (2 vertices) and, in 3D, faces
+// (4 vertices), each identified by its vertex set.  An entity is filed under
+// its smallest vertex: per vertex a chain of the entities it is the smallest
+// vertex of, holding the other vertices in increasing order, so a lookup
+// walks a handful of entries.
+struct Entities {
+  int nv;                          // vertices per entity
+  std::vector<int32_t> head;       // per mesh vertex: first entity of its chain or -1
+  std::vector<int32_t> next;       // per entity: next entity in the chain or -1
+  std::vector<int32_t> rest;       // per entity: its nv - 1 larger vertices
+  Entities(int nverts_per, int64_t n_mesh_vertices) : nv(nverts_per), head((size_t)n_mesh_vertices, -1) {}
+  int32_t size() const { return (int32_t)next.size(); }
+  // id of the entity with these vertices (sorted increasingly), added if new
+  int32_t find_or_add(const int32_t* v) {
+    for (int32_t e = head[v[0]]; e >= 0; e = next[e]) {
+      const int32_t* r = &rest[(size_t)e * (nv - 1)];
+      bool eq = true;
+      for (int j = 1; j < nv; ++j) eq = eq && r[j - 1] == v[j];
+      if (eq) return e;
+    }
+    const int32_t e = size();
+    next.push_back(head[v[0]]);
+    head[v[0]] = e;
+    for (int j = 1; j < nv; ++j) rest.push_back(v[j]);
+    return e;
+  }
+};
+
+// The nodes inside one kind of entity: per entity up to `cap` slots, each
+// holding the node's corner weights (packed, in increasing vertex order) and
+// its node number.
+struct EntityNodes {
+  int cap;
+  std::vector<uint8_t> count;
+  std::vector<uint32_t> key;
+  std::vector<int32_t> node;
+  EntityNodes(int c, int32_t n) : cap(c), count((size_t)n, 0), key((size_t)n * c), node((size_t)n * c) {}
+  // node number of the node with weights `w` in entity e, or -1 if not numbered yet
+  int32_t find(int32_t e, uint32_t w) const {
+    for (int j = 0; j < count[e]; ++j)
+      if (key[(size_t)e * cap + j] == w) return node[(size_t)e * cap + j];
+    return -1;
+  }
+  // false when the entity's slots are full: more distinct nodes than a
+  // conforming edge or face has (a twisted face)
+  bool add(int32_t e, uint32_t w, int32_t id) {
+    if (count[e] >= cap) return false;
+    const size_t j = (size_t)e * cap + count[e]++;
+    key[j] = w;
+    node[j] = id;
     return true;
   }
 };
-struct KeyHash {
-  size_t operator()(const Key& k) const {
-    uint64_t h = 1469598103934665603ull ^ (uint64_t)k.n;
-    for (int i = 0; i < k.n; ++i) {
-      h = (h ^ (uint64_t)(uint32_t)k.v[i]) * 1099511628211ull;
-      h = (h ^ (uint64_t)(uint32_t)k.w[i]) * 1099511628211ull;
+
+void sort_small(int32_t* v, uint32_t* w, int n) {  // by vertex, weights alongside
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && v[j] < v[j - 1]; --j) {
+      std::swap(v[j], v[j - 1]);
+      std::swap(w[j], w[j - 1]);
     }
-    return (size_t)(h ^ (h >> 29));
-  }
-};
-struct FaceKey {
-  int32_t v[4];
-  int n;
-  bool operator==(const FaceKey& o) const {
-    for (int i = 0; i < n; ++i)
-      if (v[i] != o.v[i]) return false;
-    return n == o.n;
-  }
-};
-struct FaceHash {
-  size_t operator()(const FaceKey& k) const {
-    uint64_t h = 1469598103934665603ull;
-    for (int i = 0; i < k.n; ++i) h = (h ^ (uint64_t)(uint32_t)k.v[i]) * 1099511628211ull;
-    return (size_t)(h ^ (h >> 31));
-  }
-};
+}
 }  // namespace
 
+// Continuous node numbering, first touch in (cell, local node) order: a node
+// is identified by the mesh vertices whose multilinear weight at it is
+// nonzero, W_v = prod_d (bit_d(v) ? m_d : k - m_d) for local node
+// (m_0, m_1, m_2), together with those weights.  Vertex nodes are indexed by
+// their vertex, nodes strictly inside a cell are new, edge and face nodes are
+// looked up in their entity's slots.
 int number_nodes(const int32_t* cells, int64_t nc, int64_t nv, int dim, int k,
                  const uint8_t* dirichlet_vertex, HostNumbering* out) {
   const int n1 = k + 1;
   const int nloc = dim == 2 ? n1 * n1 : n1 * n1 * n1;
   const int ncorner = 1 << dim;
-  // corner weights W[i][v] = prod_d (bit_d(v) ? m_d : k - m_d)
-  std::vector<int> W((size_t)nloc * ncorner);
-  std::vector<int> mi((size_t)nloc * 3);
+  const int nedge = dim == 2 ? 4 : 12, nface = dim == 3 ? 6 : 0;
+  // local edges: corner pairs differing in one bit; local faces: (axis a, side s) -> 2a + s
+  int edge_corners[12][2], edge_of[8][8];
+  {
+    int e = 0;
+    for (int a = 0; a < dim; ++a)
+      for (int v = 0; v < ncorner; ++v)
+        if (!((v >> a) & 1)) {
+          edge_corners[e][0] = v;
+          edge_corners[e][1] = v | (1 << a);
+          edge_of[v][v | (1 << a)] = edge_of[v | (1 << a)][v] = e;
+          ++e;
+        }
+  }
+  // per local node: corners with nonzero weight, those weights, its local entity
+  std::vector<int> nz((size_t)nloc), ent((size_t)nloc, -1), mi((size_t)nloc * 3);
+  std::vector<int> corner((size_t)nloc * 8);
+  std::vector<uint32_t> weight((size_t)nloc * 8);
   for (int i = 0; i < nloc; ++i) {
     int m[3] = {i % n1, (i / n1) % n1, i / (n1 * n1)};
+    if (dim == 2) m[2] = 0;
     for (int d = 0; d < 3; ++d) mi[i * 3 + d] = m[d];
+    int z = 0;
     for (int v = 0; v < ncorner; ++v) {
       int w = 1;
       for (int d = 0; d < dim; ++d) w *= ((v >> d) & 1) ? m[d] : (k - m[d]);
-      W[(size_t)i * ncorner + v] = w;
+      if (w) {
+        corner[(size_t)i * 8 + z] = v;
+        weight[(size_t)i * 8 + z] = (uint32_t)w;
+        ++z;
+      }
+    }
+    nz[i] = z;
+    if (z == 2) {
+      ent[i] = edge_of[corner[(size_t)i * 8]][corner[(size_t)i * 8 + 1]];
+    } else if (z == 4 && dim == 3) {
+      for (int a = 0; a < 3; ++a)
+        if (m[a] == 0 || m[a] == k) ent[i] = 2 * a + (m[a] == k ? 1 : 0);
     }
   }
+  // pass 1: entity numbers of every cell's edges and faces
+  Entities edges(2, nv), faces(4, nv);
+  std::vector<int32_t> cell_edge((size_t)nc * nedge), cell_face((size_t)nc * nface);
+  for (int64_t c = 0; c < nc; ++c) {
+    const int32_t* cv = cells + c * ncorner;
+    for (int e = 0; e < nedge; ++e) {
+      int32_t v[2] = {cv[edge_corners[e][0]], cv[edge_corners[e][1]]};
+      if (v[1] < v[0]) std::swap(v[0], v[1]);
+      cell_edge[(size_t)c * nedge + e] = edges.find_or_add(v);
+    }
+    for (int f = 0; f < nface; ++f) {
+      int32_t v[4];
+      int n = 0;
+      for (int u = 0; u < ncorner; ++u)
+        if (((u >> (f / 2)) & 1) == (f & 1)) v[n++] = cv[u];
+      auto cs = [&](int a, int b) {
+        if (v[b] < v[a]) std::swap(v[a], v[b]);
+      };
+      cs(0, 1), cs(2, 3), cs(0, 2), cs(1, 3), cs(1, 2);   // sorting network for 4
+      cell_face[(size_t)c * nface + f] = faces.find_or_add(v);
+    }
+  }
+  // pass 2: node numbers
+  const int ecap = std::max(k - 1, 1), fcap = std::max((k - 1) * (k - 1), 1);
+  EntityNodes enodes(ecap, edges.size()), fnodes(fcap, faces.size());
   out->cell_nodes.assign((size_t)nc * nloc, -1);
   out->owner_cell.clear();
   out->owner_local.clear();
+  {  // nodes: vertices + edge nodes + face nodes + cell interiors
+    const int64_t interior = dim == 2 ? (int64_t)(k - 1) * (k - 1) : (int64_t)(k - 1) * (k - 1) * (k - 1);
+    const int64_t est = nv + (int64_t)edges.size() * (k - 1) + (int64_t)faces.size() * (k - 1) * (k - 1) +
+                        nc * interior;
+    out->owner_cell.reserve((size_t)est);
+    out->owner_local.reserve((size_t)est);
+  }
   std::vector<int32_t> vertex_node((size_t)nv, -1);
-  std::unordered_map<Key, int32_t, KeyHash> shared;
-  shared.reserve((size_t)nc * (nloc - 1) / 2 + 16);
   int64_t next = 0;
+  auto fresh = [&](int64_t c, int i) {
+    out->owner_cell.push_back((int32_t)c);
+    out->owner_local.push_back(i);
+    return (int32_t)next++;
+  };
   for (int64_t c = 0; c < nc; ++c) {
     const int32_t* cv = cells + c * ncorner;
     for (int i = 0; i < nloc; ++i) {
-      int nz = 0;
-      int32_t vv[8];
-      int32_t ww[8];
-      for (int v = 0; v < ncorner; ++v) {
-        int w = W[(size_t)i * ncorner + v];
-        if (w) {
-          vv[nz] = cv[v];
-          ww[nz] = w;
-          ++nz;
-        }
-      }
+      const int z = nz[i];
       int32_t id;
-      if (nz == 1) {
-        int32_t& slot = vertex_node[vv[0]];
-        if (slot < 0) {
-          slot = (int32_t)next++;
-          out->owner_cell.push_back((int32_t)c);
-          out->owner_local.push_back(i);
-        }
+      if (z == 1) {
+        int32_t& slot = vertex_node[cv[corner[(size_t)i * 8]]];
+        if (slot < 0) slot = fresh(c, i);
         id = slot;
-      } else if (nz == ncorner) {
-        id = (int32_t)next++;
-        out->owner_cell.push_back((int32_t)c);
-        out->owner_local.push_back(i);
+      } else if (z == ncorner) {
+        id = fresh(c, i);
       } else {
-        Key key;
-        key.n = nz;
-        int order[4] = {0, 1, 2, 3};
-        std::sort(order, order + nz, [&](int a, int b) { return vv[a] < vv[b]; });
-        for (int j = 0; j < nz; ++j) {
-          key.v[j] = vv[order[j]];
-          key.w[j] = ww[order[j]];
+        int32_t v[4];
+        uint32_t w[4];
+        for (int j = 0; j < z; ++j) {
+          v[j] = cv[corner[(size_t)i * 8 + j]];
+          w[j] = weight[(size_t)i * 8 + j];
         }
-        auto it = shared.find(key);
-        if (it == shared.end()) {
-          id = (int32_t)next++;
-          shared.emplace(key, id);
-          out->owner_cell.push_back((int32_t)c);
-          out->owner_local.push_back(i);
-        } else {
-          id = it->second;
+        sort_small(v, w, z);
+        uint32_t packed = 0;
+        for (int j = 0; j < z; ++j) packed |= w[j] << (8 * j);
+        EntityNodes& en = z == 2 ? enodes : fnodes;
+        const int32_t e = z == 2 ? cell_edge[(size_t)c * nedge + ent[i]] : cell_face[(size_t)c * nface + ent[i]];
+        id = en.find(e, packed);
+        if (id < 0) {
+          id = fresh(c, i);
+          if (!en.add(e, packed, id)) {
+            set_error("non-conforming mesh: an edge or face is shared with inconsistent vertex order");
+            return NNMG_BAD_MESH;
+          }
         }
       }
       out->cell_nodes[(size_t)c * nloc + i] = id;
@@ -266,31 +344,26 @@ int number_nodes(const int32_t* cells, int64_t nc, int64_t nv, int dim, int k,
   out->n_nodes = next;
   out->constrained.assign((size_t)next, 0);
   if (!dirichlet_vertex) return NNMG_OK;
-  // boundary faces: faces of exactly one cell
-  std::unordered_map<FaceKey, int32_t, FaceHash> faces;
-  faces.reserve((size_t)nc * dim * 2);
-  auto face_key = [&](int64_t c, int a, int s) {
-    FaceKey f;
-    f.n = 0;
-    for (int v = 0; v < ncorner; ++v)
-      if (((v >> a) & 1) == s) f.v[f.n++] = cells[c * ncorner + v];
-    std::sort(f.v, f.v + f.n);
-    return f;
+  // boundary faces (edges in 2D): those of exactly one cell
+  const Entities& bent = dim == 3 ? faces : edges;
+  std::vector<int32_t> uses((size_t)bent.size(), 0);
+  auto boundary_entity = [&](int64_t c, int a, int side) {
+    if (dim == 3) return cell_face[(size_t)c * nface + 2 * a + side];
+    return cell_edge[(size_t)c * nedge + edge_of[side << a][(side << a) | (1 << (1 - a))]];
   };
   for (int64_t c = 0; c < nc; ++c)
     for (int a = 0; a < dim; ++a)
-      for (int s = 0; s < 2; ++s) faces[face_key(c, a, s)] += 1;
+      for (int side = 0; side < 2; ++side) uses[boundary_entity(c, a, side)]++;
   for (int64_t c = 0; c < nc; ++c) {
     for (int a = 0; a < dim; ++a) {
-      for (int s = 0; s < 2; ++s) {
-        FaceKey f = face_key(c, a, s);
-        if (faces[f] != 1) continue;
+      for (int side = 0; side < 2; ++side) {
+        if (uses[boundary_entity(c, a, side)] != 1) continue;
         bool flagged = true;
-        for (int j = 0; j < f.n; ++j) flagged = flagged && dirichlet_vertex[f.v[j]];
+        for (int u = 0; u < ncorner; ++u)
+          if (((u >> a) & 1) == side) flagged = flagged && dirichlet_vertex[cells[c * ncorner + u]];
         if (!flagged) continue;
         for (int i = 0; i < nloc; ++i)
-          if (mi[i * 3 + a] == s * k)
-            out->constrained[out->cell_nodes[(size_t)c * nloc + i]] = 1;
+          if (mi[i * 3 + a] == side * k) out->constrained[out->cell_nodes[(size_t)c * nloc + i]] = 1;
       }
     }
   }
@@ -373,8 +446,11 @@ void build_buckets(const double* vertices, const int32_t* cells, int64_t nc, int
 }
 
 // ------------------------------------------------------------ dense SPD
-// Blocked right-looking Cholesky (lower, row-major) with the trailing update
-// split over host threads, then A^-1 column by column from L and L^T.
+// Blocked right-looking Cholesky A = L L^T (lower, row-major) with the
+// trailing update split over host threads; then W = L^-1 and A^-1 = W^T W.
+// Both products run on 32-column blocks of W whose rows are contiguous, so
+// the inner loops are vectorizable updates over a block's columns that reuse
+// each loaded factor entry 32 times.
 bool dense_spd_inverse(std::vector<double>& a, int n, std::vector<double>* inv) {
   const int nb = 64;
   unsigned nt = std::max(1u, std::thread::hardware_concurrency());
@@ -416,38 +492,82 @@ bool dense_spd_inverse(std::vector<double>& a, int n, std::vector<double>* inv) 
         ri[j] = t / rj[j];
       }
     });
-    // trailing update A22 -= L21 L21^T (lower triangle)
-    par(k1, n, [&](int64_t i) {
-      double* ri = A + (size_t)i * n;
-      for (int64_t j = k1; j <= i; ++j) {
-        const double* rj = A + (size_t)j * n;
-        double t = 0.0;
-        for (int p = k0; p < k1; ++p) t += ri[p] * rj[p];
-        ri[j] -= t;
+    // trailing update A22 -= L21 L21^T (lower triangle) in 4 x 4 blocks of
+    // rows: every loaded panel entry feeds four multiply-adds
+    const int nrb = (n - k1 + 3) / 4;
+    par(0, nrb, [&](int64_t ib) {
+      const int i0 = k1 + 4 * (int)ib, ni = std::min(4, n - i0);
+      const double* xr[4];
+      for (int r = 0; r < 4; ++r) xr[r] = A + (size_t)(i0 + std::min(r, ni - 1)) * n;
+      for (int j0 = k1; j0 < i0 + ni; j0 += 4) {
+        const int nj = std::min(4, n - j0);
+        const double* yr[4];
+        for (int c = 0; c < 4; ++c) yr[c] = A + (size_t)(j0 + std::min(c, nj - 1)) * n;
+        double acc[4][4] = {{0.0}};
+        for (int p = k0; p < k1; ++p) {
+          const double x0 = xr[0][p], x1 = xr[1][p], x2 = xr[2][p], x3 = xr[3][p];
+          const double y[4] = {yr[0][p], yr[1][p], yr[2][p], yr[3][p]};
+          for (int c = 0; c < 4; ++c) {
+            acc[0][c] += x0 * y[c];
+            acc[1][c] += x1 * y[c];
+            acc[2][c] += x2 * y[c];
+            acc[3][c] += x3 * y[c];
+          }
+        }
+        for (int r = 0; r < ni; ++r)
+          for (int c = 0; c < nj; ++c)
+            if (j0 + c <= i0 + r) A[(size_t)(i0 + r) * n + j0 + c] -= acc[r][c];
       }
     });
   }
-  // U = L^T (row-major) for the backward solves
-  std::vector<double> U((size_t)n * n, 0.0);
-  par(0, n, [&](int64_t i) {
-    for (int j = 0; j <= i; ++j) U[(size_t)j * n + i] = A[(size_t)i * n + j];
+  // W = L^-1 by blocks of B columns: block jb holds rows jb*B .. n-1 (rows
+  // above are zero), W[i][j] = (delta_ij - sum_{p<i} L[i][p] W[p][j]) / L[i][i]
+  constexpr int B = 32;
+  const int nblk = (n + B - 1) / B;
+  std::vector<std::vector<double>> Wb((size_t)nblk);
+  par(0, nblk, [&](int64_t jb) {
+    const int c0 = (int)jb * B, w = std::min(B, n - c0);
+    std::vector<double>& W = Wb[(size_t)jb];
+    W.assign((size_t)(n - c0) * B, 0.0);
+    for (int i = c0; i < n; ++i) {
+      double acc[B];                          // row i of the block, kept in registers
+      for (int j = 0; j < B; ++j) acc[j] = (i - c0 == j && j < w) ? 1.0 : 0.0;
+      const double* li = A + (size_t)i * n;
+      for (int p = c0; p < i; ++p) {
+        const double l = li[p];
+        const double* wp = &W[(size_t)(p - c0) * B];
+        for (int j = 0; j < B; ++j) acc[j] -= l * wp[j];
+      }
+      double* wi = &W[(size_t)(i - c0) * B];
+      const double d = li[i];
+      for (int j = 0; j < B; ++j) wi[j] = acc[j] / d;
+    }
   });
+  // A^-1 = W^T W: block (ja, jb), ja <= jb, sums rows i >= jb*B; mirrored
+  std::vector<std::pair<int, int>> pairs;
+  for (int jb = 0; jb < nblk; ++jb)
+    for (int ja = 0; ja <= jb; ++ja) pairs.emplace_back(ja, jb);
   inv->assign((size_t)n * n, 0.0);
-  par(0, n, [&](int64_t col) {
-    std::vector<double> y((size_t)n, 0.0);
-    for (int64_t i = col; i < n; ++i) {       // L y = e_col
-      const double* ri = A + (size_t)i * n;
-      double t = (i == col) ? 1.0 : 0.0;
-      for (int64_t p = col; p < i; ++p) t -= ri[p] * y[p];
-      y[i] = t / ri[i];
+  par(0, (int64_t)pairs.size(), [&](int64_t t) {
+    const int ja = pairs[(size_t)t].first, jb = pairs[(size_t)t].second;
+    double acc[B][B];
+    for (int a = 0; a < B; ++a)
+      for (int b = 0; b < B; ++b) acc[a][b] = 0.0;
+    for (int i = jb * B; i < n; ++i) {
+      const double* wa = &Wb[(size_t)ja][(size_t)(i - ja * B) * B];
+      const double* wb = &Wb[(size_t)jb][(size_t)(i - jb * B) * B];
+      for (int a = 0; a < B; ++a) {
+        const double x = wa[a];
+        for (int b = 0; b < B; ++b) acc[a][b] += x * wb[b];
+      }
     }
-    for (int64_t i = n - 1; i >= 0; --i) {    // L^T x = y
-      const double* ui = U.data() + (size_t)i * n;
-      double t = y[i];
-      for (int64_t p = i + 1; p < n; ++p) t -= ui[p] * y[p];
-      y[i] = t / ui[i];
-    }
-    for (int64_t i = 0; i < n; ++i) (*inv)[(size_t)i * n + col] = y[i];
+    const int na = std::min(B, n - ja * B), nbb = std::min(B, n - jb * B);
+    for (int a = 0; a < na; ++a)
+      for (int b = 0; b < nbb; ++b) {
+        const int r = ja * B + a, c = jb * B + b;
+        (*inv)[(size_t)r * n + c] = acc[a][b];
+        (*inv)[(size_t)c * n + r] = acc[a][b];
+      }
   });
   return true;
 }

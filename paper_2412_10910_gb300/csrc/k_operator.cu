@@ -16,6 +16,7 @@
 // Dirichlet nodes carry index -1: read as 0, never written.  y must be zero on
 // entry (scatter is atomic).
 #include <algorithm>
+#include <type_traits>
 
 #include "dword.h"
 #include "nnmg_internal.h"
@@ -762,7 +763,9 @@ cudaError_t run_reg2(const DevLevel& L, const float* metric, const float* x, flo
 // units = -2 for its paired FP32 form (even
 // nrhs, 8-byte aligned vectors; otherwise the unpaired one runs), units > 0
 // for the shared-memory kernel with that many units per block (autotuner
-// choices), units = 0 for the default (the register kernel where it applies).
+// choices), units = 0 for the default: the register kernel where it applies
+// in FP32 and FP64, the shared-memory kernel in double-word arithmetic (whose
+// register kernel, at 255 registers, measured 1.9x slower on 3D Q2).
 template <typename T>
 bool reg_eligible(const DevLevel& L) {
   return L.ncomp == 1 && (L.dim == 2 || L.k <= 2);
@@ -783,7 +786,8 @@ cudaError_t launch_operator_impl(const DevLevel& L, const typename io_of<T>::typ
 #undef NNMG_REG2
     }
   }
-  if (reg_eligible<T>(L) && units <= 0) {
+  constexpr bool reg_default = !std::is_same<T, dw>::value;
+  if (reg_eligible<T>(L) && (units < 0 || (units == 0 && reg_default))) {
 #define NNMG_REG(D, K) if (L.dim == D && L.k == K) return run_reg<D, K, T>(L, m, x, y, nrhs, s);
     NNMG_REG(2, 1) NNMG_REG(2, 2) NNMG_REG(2, 3) NNMG_REG(2, 4) NNMG_REG(3, 1) NNMG_REG(3, 2)
 #undef NNMG_REG

@@ -5,6 +5,7 @@
 // kernels on internal buffers; after a first eager run they are captured once
 // per (precision or mode, nrhs) into a CUDA graph and replayed.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <map>
@@ -44,6 +45,8 @@ struct nnmg_handle {
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (kind, prec/mode, nrhs)
   std::map<std::tuple<int, int, int>, int> runs;
   std::map<std::tuple<int, int, int>, int> op_units;  // (level, precision, nrhs) -> units
+  // wall seconds of the setup phases (see nnmg_setup_seconds in nnmg.h)
+  double setup_s[NNMG_SETUP_PHASES] = {0};
   // continuous batching state
   int batch_mode = -1, batch_slots = 0;
   cudaEvent_t batch_ev = nullptr;
@@ -51,6 +54,10 @@ struct nnmg_handle {
 };
 
 namespace {
+
+double wall_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 template <typename T>
 cudaError_t dalloc(nnmg_handle* h, T** p, size_t count, bool work = false) {
@@ -533,8 +540,11 @@ int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStrea
       return NNMG_INVALID_ARG;
     }
   }
+  const double t0 = wall_seconds();
   int rc = number_nodes(d.cells, d.n_cells, d.n_vertices, d.dim, L.k, d.dirichlet_vertex, &L.num);
   if (rc != NNMG_OK) return rc;
+  const double t1 = wall_seconds();
+  h->setup_s[0] += t1 - t0;
   L.n_nodes = L.num.n_nodes;
   L.rows = L.n_nodes * L.ncomp;
   L.n_free_nodes = 0;
@@ -583,6 +593,7 @@ int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStrea
   CK(launch_diag(L, o.lambda, o.mu, s));
   CK(launch_finalize_diag(L.diag64, L.row_free, L.dinv64, L.dinv32, L.rows, s));
   CK(cudaStreamSynchronize(s));
+  h->setup_s[1] += wall_seconds() - t1;
   return NNMG_OK;
 }
 
@@ -774,19 +785,27 @@ int nnmg_setup_hierarchy(const nnmg_level_desc* levels, int n_levels, const nnmg
     h->lv.resize(n_levels);
     int rc = NNMG_OK;
     for (int l = 0; l < n_levels && rc == NNMG_OK; ++l) rc = setup_level(h, levels[l], h->lv[l], s);
+    double t = wall_seconds();
     for (int l = 1; l < n_levels && rc == NNMG_OK; ++l) rc = setup_transfer(h, l, s);
+    h->setup_s[2] = wall_seconds() - t;
+    t += h->setup_s[2];
     for (int l = 0; l + 1 < n_levels && rc == NNMG_OK; ++l) rc = setup_gather(h, h->lv[l]);
+    h->setup_s[3] = wall_seconds() - t;
+    t += h->setup_s[3];
     for (int l = 1; l < n_levels && rc == NNMG_OK; ++l) {
       rc = lanczos(h, h->lv[l], s);
       DevLevel& L = h->lv[l];
       L.cheb_b = h->opt.eig_safety * L.lam_max;
       L.cheb_a = L.cheb_b / h->opt.smoothing_range;
     }
+    h->setup_s[4] = wall_seconds() - t;
+    t += h->setup_s[4];
     if (rc == NNMG_OK) rc = setup_coarse(h, h->lv[0], s);
     if (rc == NNMG_OK && cudaStreamSynchronize(s) != cudaSuccess) {
       set_error("setup: stream synchronize failed");
       rc = NNMG_CUDA_ERROR;
     }
+    h->setup_s[5] = wall_seconds() - t;
     if (rc != NNMG_OK) {
       std::string msg = get_error();
       destroy_impl(h);
@@ -891,6 +910,15 @@ int nnmg_transfer_points(const nnmg_handle* h, int fine_level, int32_t* cell, do
   const DevLevel& F = h->lv[fine_level];
   if (cell) std::memcpy(cell, F.h_loc_cell.data(), F.h_loc_cell.size() * sizeof(int32_t));
   if (xi) std::memcpy(xi, F.h_loc_xi.data(), F.h_loc_xi.size() * sizeof(double));
+  return NNMG_OK;
+}
+
+int nnmg_setup_seconds(const nnmg_handle* h, double* seconds) {
+  if (!h || !seconds) {
+    set_error("nnmg_setup_seconds: null handle or pointer");
+    return NNMG_INVALID_ARG;
+  }
+  for (int i = 0; i < NNMG_SETUP_PHASES; ++i) seconds[i] = h->setup_s[i];
   return NNMG_OK;
 }
 

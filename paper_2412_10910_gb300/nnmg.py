@@ -151,6 +151,16 @@ def nnmg_transfer_points(h, fine_level, dim):
     return cell, xi
 
 
+SETUP_PHASES = ("numbering", "level_geometry", "point_location", "gather_lists", "lanczos",
+                "coarse_inverse")
+
+
+def nnmg_setup_seconds(h):
+    out = np.zeros(len(SETUP_PHASES))
+    _check(_lib.nnmg_setup_seconds(h, out.ctypes.data), "nnmg_setup_seconds")
+    return dict(zip(SETUP_PHASES, out.tolist()))
+
+
 def nnmg_operator_choice(h, level, precision, nrhs):
     out = C.c_int(0)
     _check(_lib.nnmg_operator_choice(h, level, precision, nrhs, C.byref(out)), "nnmg_operator_choice")
@@ -336,6 +346,10 @@ class Hierarchy:
 
     def eigen_estimates(self):
         return nnmg_eigen_estimates(self.h)
+
+    def setup_seconds(self):
+        """Wall seconds of the setup phases, by name."""
+        return nnmg_setup_seconds(self.h)
 
     def operator_choice(self, level, precision, nrhs):
         """-1 register kernel, -2 paired FP32 register kernel, U > 0 shared-memory

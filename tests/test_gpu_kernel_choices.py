@@ -117,3 +117,34 @@ def test_vcycle_and_pcg_with_variant(choice, monkeypatch):
             assert np.all(err <= 1e-7), err
     finally:
         H.close()
+
+
+def test_operator_choice_and_setup_phases_are_reported(monkeypatch):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import time
+    from paper_2412_10910_gb300 import _abi, nnmg
+    name = "c2_q2_3lev"
+    levels, O = oracle_case(name)
+    monkeypatch.setenv("NNMG_OP_CHOICE", "-1")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H = gpu_case(name, levels)
+    wall = time.perf_counter() - t0
+    try:
+        phases = H.setup_seconds()
+        assert list(phases) == list(nnmg.SETUP_PHASES)
+        assert all(v >= 0.0 for v in phases.values())
+        assert 0.0 < sum(phases.values()) <= wall
+        nrhs = CASES[name][5]
+        top = len(O.levels) - 1
+        assert H.operator_choice(top, _abi.F64, nrhs) == 0          # not used yet
+        x = torch.zeros(H.rows(top), nrhs, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        H.apply(top, x, y)
+        assert H.operator_choice(top, _abi.F64, nrhs) == -1
+        for bad in [(top + 1, _abi.F64, nrhs), (top, 7, nrhs), (top, _abi.F64, 0), (-1, _abi.F64, 1)]:
+            with pytest.raises(nnmg.NNMGError):
+                H.operator_choice(*bad)
+    finally:
+        H.close()
