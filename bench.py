@@ -159,12 +159,14 @@ def replica_aggregate(local_ms, local_units, world, reduce_max, reduce_sum):
 
 
 def kernels_per_solve(n_levels, cheb, iters):
-    """Kernel launches of one PCG solve: init 2, per iteration the V-cycle
-    (per level above the coarsest: 1 + 2(m-1) pre, 2 residual, 2 restriction,
-    1 prolongation, 2m post; 1 coarse solve) plus 9 CG kernels (cast, two dots,
-    beta, p, operator, alpha, update, check)."""
+    """Kernel launches of one PCG solve run as the device-side graph loop:
+    init 2 and the loop's arming kernel, per iteration the V-cycle (per level
+    above the coarsest: 1 + 2(m-1) pre, 2 residual, 2 restriction,
+    1 prolongation, 2m post; the coarse solve and its fixed-order segment sum),
+    8 CG kernels (two dots, beta, p, operator, alpha, update with the FP32 copy
+    of r, check) and the loop's re-arming kernel."""
     per_level = 1 + 2 * (cheb - 1) + 2 + 2 + 1 + 2 * cheb
-    return 2 + iters * ((n_levels - 1) * per_level + 1 + 9)
+    return 3 + iters * ((n_levels - 1) * per_level + 2 + 8 + 1)
 
 
 def cpu_baseline_sample(nrhs_sample=8, steps=1, warmup=0):
@@ -420,6 +422,9 @@ def main():
                     default=None, help="run only one timed section (for profiler launch lists), "
                     "or the serving mix")
     ap.add_argument("--requests", type=int, default=2000, help="serving mix: number of requests")
+    ap.add_argument("--config", default=CONFIG, choices=["c1_2d_q1", "c2_3d_q2", "c3_3d_q4_deformed"],
+                    help="Poisson configuration of the --only sections (the full line always "
+                         "measures config 2)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -459,8 +464,9 @@ def main():
     def sum_over_ranks(v):
         return v if world == 1 else _reduce(v, dist.ReduceOp.SUM)
 
-    cfg = CONFIGS[CONFIG]
-    levels = config_levels(CONFIG)
+    name = args.config if args.only else CONFIG
+    cfg = CONFIGS[name]
+    levels = config_levels(name)
     nrhs = cfg["nrhs"]
     H = nnmg.Hierarchy(levels, cfg["degree"], 1, cheb_degree=cfg["cheb"], max_nrhs=16)
     top = H.n_levels - 1

@@ -161,6 +161,15 @@ int nnmg_quadrature_points(const nnmg_handle* h, int level, double* xq);
  * cell [n_free_fine], xi [n_free_fine][dim] (clamped to [0,1]^d). */
 int nnmg_transfer_points(const nnmg_handle* h, int fine_level, int32_t* cell, double* xi);
 
+/* Whether nnmg_pcg_solve / nnmg_pcg_solve_host for (mode, nrhs) now run as
+ * one device-side graph loop (a CUDA graph WHILE node around one PCG
+ * iteration; the host waits once per solve): *state = 1 built, 0 not built
+ * yet (it is built on the second solve, after the first has tuned and
+ * captured the iteration), -1 could not be built (the host-driven loop runs).
+ * The environment variable NNMG_DEVICE_LOOP=0 keeps the host-driven loop.
+ * No counterpart in the paper.  INVALID_ARG for a null handle or pointer. */
+int nnmg_pcg_device_loop(const nnmg_handle* h, int mode, int nrhs, int* state);
+
 /* Wall seconds of the setup phases of this hierarchy (no counterpart in the
  * paper, which does not time setup): seconds[NNMG_SETUP_PHASES] =
  * {0 node numbering (host), 1 per-level device geometry: metric terms,

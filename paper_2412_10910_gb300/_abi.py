@@ -39,6 +39,7 @@ PROTOTYPES = {
     "nnmg_cell_nodes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_quadrature_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_transfer_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "nnmg_pcg_device_loop": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "nnmg_setup_seconds": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nnmg_operator_choice": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "nnmg_eigen_estimates": (C.c_int, [C.c_void_p, C.c_void_p]),

@@ -38,6 +38,11 @@ __device__ __forceinline__ void lagrange1d(const Basis1D<T>& B, T xi, T* L) {
   }
 }
 
+// Fine points of a coarse cell are handled in chunks of kChunk: a cell holds
+// about (refinement ratio)^d points, ~66-68 for the 2.1-2.2x coarsening of the
+// configurations, so one chunk (one gather round, two barriers) covers it.
+constexpr int kChunk = 128;
+
 template <int D, int K, typename T>
 __global__ void prolong_kernel(const int32_t* __restrict__ coarse_cell_nodes,
                                const T* __restrict__ xc, T* __restrict__ xf,
@@ -55,42 +60,47 @@ __global__ void prolong_kernel(const int32_t* __restrict__ coarse_cell_nodes,
     su[e] = node >= 0 ? xc[(int64_t)node * nch + ch] : T(0);
   }
   __syncthreads();
+  __shared__ T sL[kChunk][D][N];      // 1D bases of the chunk's points
   const int p0 = cell_pt_start[c], p1 = cell_pt_start[c + 1];
-  for (int e = threadIdx.x; e < (p1 - p0) * nch; e += blockDim.x) {
-    const int pl = e / nch, ch = e - pl * nch;
-    const int p = p0 + pl;
-    T L[D][N];
-#pragma unroll
-    for (int d = 0; d < D; ++d) lagrange1d<N, T>(B, pt_xi[(int64_t)p * D + d], L[d]);
-    T val = 0;
-    if constexpr (D == 2) {
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        T s = 0;
-#pragma unroll
-        for (int i = 0; i < N; ++i) s += L[0][i] * su[(i + N * j) * nch + ch];
-        val += L[1][j] * s;
-      }
-    } else {
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        T s1 = 0;
+  for (int q0 = p0; q0 < p1; q0 += kChunk) {
+    const int np = min(kChunk, p1 - q0);
+    __syncthreads();                   // the previous chunk's readers are done
+    for (int t = threadIdx.x; t < np * D; t += blockDim.x) {
+      const int pp = t / D, d = t - pp * D;
+      lagrange1d<N, T>(B, pt_xi[(int64_t)(q0 + pp) * D + d], sL[pp][d]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * nch; e += blockDim.x) {
+      const int pl = e / nch, ch = e - pl * nch;
+      const T(&L)[D][N] = sL[pl];
+      T val = 0;
+      if constexpr (D == 2) {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          T s0 = 0;
+          T s = 0;
 #pragma unroll
-          for (int i = 0; i < N; ++i) s0 += L[0][i] * su[(i + N * j + N * N * l) * nch + ch];
-          s1 += L[1][j] * s0;
+          for (int i = 0; i < N; ++i) s += L[0][i] * su[(i + N * j) * nch + ch];
+          val += L[1][j] * s;
         }
-        val += L[2][l] * s1;
+      } else {
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          T s1 = 0;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            T s0 = 0;
+#pragma unroll
+            for (int i = 0; i < N; ++i) s0 += L[0][i] * su[(i + N * j + N * N * l) * nch + ch];
+            s1 += L[1][j] * s0;
+          }
+          val += L[2][l] * s1;
+        }
       }
+      T* o = xf + (int64_t)pt_node[q0 + pl] * nch + ch;
+      *o += val;
     }
-    T* o = xf + (int64_t)pt_node[p] * nch + ch;
-    *o += val;
   }
 }
-
-constexpr int kChunk = 64;
 
 template <int D, int K, typename T>
 __global__ void restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
@@ -146,64 +156,57 @@ __global__ void restrict2_kernel(const T* __restrict__ buf, const int32_t* __res
   rc[e] = s;
 }
 
-// z[free_i] = sum_j Ainv[i][j] r[free_j] in FP64: one warp per free row, 8 rows
-// per block; the gathered right-hand sides pass through shared memory in tiles
-// of kCoarseTile rows, stored column-major so that lanes read distinct banks.
-constexpr int kCoarseRows = 8;
-constexpr int kCoarseTile = 256;
+// z[free_i] = sum_j Ainv[i][j] r[free_j] in FP64.  Every lane owns one
+// (row, right-hand side) pair: a warp covers 32 / npad rows (npad = nrhs
+// rounded up to a power of two), a block kCoarseWarps warps.  The gathered
+// right-hand sides of a tile of kCoarseTile columns pass through shared
+// memory as [column][npad] (lanes of one row read consecutive banks, lanes of
+// one right-hand side the same word), and every lane accumulates its row's
+// products over the tile with four independent chains: no cross-lane sums.
+constexpr int kCoarseWarps = 8;
+constexpr int kCoarseTile = 128;
 
 // The column range of every row is split over gridDim.y segments; segment s
 // writes partial[s][row][rhs] and coarse_sum_kernel adds the segments in order
 // (deterministic).  With gridDim.y == 1 the kernel writes z directly.
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(32 * kCoarseRows) coarse_solve_kernel(
+__global__ void __launch_bounds__(32 * kCoarseWarps) coarse_solve_kernel(
     const double* __restrict__ Ainv, const int32_t* __restrict__ rows, int n,
-    const TI* __restrict__ r, TO* __restrict__ z, int nrhs, double* __restrict__ partial) {
-  __shared__ double sr[kMaxRhs * kCoarseTile];
+    const TI* __restrict__ r, TO* __restrict__ z, int nrhs, int npad,
+    double* __restrict__ partial) {
+  __shared__ double sr[kCoarseTile * kMaxRhs];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kCoarseRows + warp;
+  const int rpw = 32 / npad;                       // rows per warp
+  const int q = lane % npad;
+  const int i = (blockIdx.x * kCoarseWarps + warp) * rpw + lane / npad;
+  const bool own = q < nrhs && i < n;
   const int seg = (n + gridDim.y - 1) / gridDim.y;
   const int jb = blockIdx.y * seg, je = min(n, jb + seg);
-  double acc[kMaxRhs];
-#pragma unroll
-  for (int q = 0; q < kMaxRhs; ++q) acc[q] = 0.0;
+  const double* arow = Ainv + (int64_t)(own ? i : 0) * n;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int j0 = jb; j0 < je; j0 += kCoarseTile) {
     const int nt = min(kCoarseTile, je - j0);
-    for (int t = threadIdx.x; t < nt * nrhs; t += blockDim.x) {
-      const int jj = t / nrhs, q = t - jj * nrhs;
-      sr[q * kCoarseTile + jj] = (double)r[(int64_t)rows[j0 + jj] * nrhs + q];
+    for (int t = threadIdx.x; t < nt * npad; t += blockDim.x) {
+      const int jj = t / npad, qq = t - jj * npad;
+      sr[t] = qq < nrhs ? (double)r[(int64_t)rows[j0 + jj] * nrhs + qq] : 0.0;
     }
     __syncthreads();
-    if (i < n) {
-      const double* arow = Ainv + (int64_t)i * n + j0;
-      for (int jj = lane; jj < nt; jj += 32) {
-        const double a = arow[jj];
+    if (own) {
+      int jj = 0;
+      for (; jj + 4 <= nt; jj += 4) {
 #pragma unroll
-        for (int q = 0; q < kMaxRhs; ++q)
-          if (q < nrhs) acc[q] += a * sr[q * kCoarseTile + jj];
+        for (int u = 0; u < 4; ++u) acc[u] += arow[j0 + jj + u] * sr[(jj + u) * npad + q];
       }
+      for (; jj < nt; ++jj) acc[0] += arow[j0 + jj] * sr[jj * npad + q];
     }
     __syncthreads();
   }
-  if (i >= n) return;
-#pragma unroll
-  for (int q = 0; q < kMaxRhs; ++q) {
-    if (q < nrhs) {
-      double v = acc[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[q] = v;
-    }
-  }
-  if (lane == 0) {
-    if (gridDim.y == 1) {
-      const int64_t ri = (int64_t)rows[i] * nrhs;
-      for (int q = 0; q < nrhs; ++q) z[ri + q] = (TO)acc[q];
-    } else {
-      double* pp = partial + ((int64_t)blockIdx.y * n + i) * kMaxRhs;
-      for (int q = 0; q < nrhs; ++q) pp[q] = acc[q];
-    }
-  }
+  if (!own) return;
+  const double v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  if (gridDim.y == 1)
+    z[(int64_t)rows[i] * nrhs + q] = (TO)v;
+  else
+    partial[((int64_t)blockIdx.y * n + i) * kMaxRhs + q] = v;
 }
 
 template <typename TO>
@@ -237,6 +240,23 @@ const double* xi_of<double>(const DevLevel& L) { return L.pt_xi64; }
 template <>
 const float* xi_of<float>(const DevLevel& L) { return L.pt_xi32; }
 
+// Opt a kernel in to `dyn` bytes of dynamic shared memory when its static
+// and dynamic shared memory together exceed the default 48 KB per block;
+// `granted` remembers the largest size already allowed for this kernel.
+template <typename F>
+cudaError_t allow_smem(F kern, size_t dyn, size_t* granted) {
+  if (dyn <= *granted) return cudaSuccess;
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kern);
+  if (e != cudaSuccess) return e;
+  if (dyn + a.sharedSizeBytes > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  *granted = dyn;
+  return cudaSuccess;
+}
+
 template <int D, int K, typename T>
 cudaError_t prolong_dk(const DevLevel& f, const DevLevel& c, const T* xc, T* xf, int nch,
                        cudaStream_t s) {
@@ -246,12 +266,9 @@ cudaError_t prolong_dk(const DevLevel& f, const DevLevel& c, const T* xc, T* xf,
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const size_t smem = (size_t)NL * nch * sizeof(T);
   auto kern = prolong_kernel<D, K, T>;
-  static size_t smem_set = 48 * 1024;
-  if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    smem_set = smem;
-  }
+  static size_t granted = 0;
+  cudaError_t e = allow_smem(kern, smem, &granted);
+  if (e != cudaSuccess) return e;
   kern<<<(unsigned)c.n_cells, 128, smem, s>>>(c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node,
                                               xi_of<T>(f), nch, B);
   return cudaGetLastError();
@@ -265,10 +282,13 @@ cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* rc
   constexpr int N = K + 1;
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const size_t smem = (size_t)kChunk * nch * sizeof(T);
+  auto kern = restrict1_kernel<D, K, T>;
+  static size_t granted = 0;
+  cudaError_t e = allow_smem(kern, smem, &granted);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)c.n_cells, (unsigned)((NL * nch + 255) / 256));
-  restrict1_kernel<D, K, T><<<grid, 256, smem, s>>>(rf, scratch, f.cell_pt_start, f.pt_node,
-                                                    xi_of<T>(f), nch, B);
-  cudaError_t e = cudaGetLastError();
+  kern<<<grid, 256, smem, s>>>(rf, scratch, f.cell_pt_start, f.pt_node, xi_of<T>(f), nch, B);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = c.n_nodes * nch;
   restrict2_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(scratch, c.gather_start,
@@ -422,12 +442,9 @@ cudaError_t gc_prolong_dk(const DevLevel& f, const DevLevel& c, const T* xc, T* 
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const size_t smem = 3 * (size_t)NL * nch * sizeof(T);
   auto kern = gc_prolong_kernel<D, K, T>;
-  static size_t smem_set = 48 * 1024;
-  if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    smem_set = smem;
-  }
+  static size_t granted = 0;
+  cudaError_t e = allow_smem(kern, smem, &granted);
+  if (e != cudaSuccess) return e;
   kern<<<(unsigned)c.n_cells, 128, smem, s>>>(c.cell_nodes, xc, xf, f.gc_children, f.cell_nodes,
                                               f.owner_cell, f.owner_local, nch, gc_tables<T>(K));
   return cudaGetLastError();
@@ -440,15 +457,12 @@ cudaError_t gc_restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T*
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const size_t smem = 3 * (size_t)NL * nch * sizeof(T);
   auto kern = gc_restrict1_kernel<D, K, T>;
-  static size_t smem_set = 48 * 1024;
-  if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    smem_set = smem;
-  }
+  static size_t granted = 0;
+  cudaError_t e = allow_smem(kern, smem, &granted);
+  if (e != cudaSuccess) return e;
   kern<<<(unsigned)c.n_cells, 128, smem, s>>>(rf, scratch, f.gc_children, f.cell_nodes,
                                               f.owner_cell, f.owner_local, nch, gc_tables<T>(K));
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = c.n_nodes * nch;
   restrict2_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(scratch, c.gather_start,
@@ -504,13 +518,16 @@ template <typename TI, typename TO>
 cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs, cudaStream_t s) {
   if (L.n_free_rows == 0) return cudaSuccess;
   const int n = L.n_free_rows;
-  const unsigned blocks = (unsigned)((n + kCoarseRows - 1) / kCoarseRows);
+  int npad = 1;
+  while (npad < nrhs) npad *= 2;
+  const int rows_per_block = kCoarseWarps * (32 / npad);
+  const unsigned blocks = (unsigned)((n + rows_per_block - 1) / rows_per_block);
   // enough segments for ~4 blocks per SM, each segment at least one tile long
   int nseg = (int)std::min<int64_t>(kCoarseMaxSegments, std::max<int64_t>(1, (4 * 152) / blocks));
   nseg = std::max(1, std::min(nseg, (n + kCoarseTile - 1) / kCoarseTile));
   if (!L.coarse_partial) nseg = 1;
-  coarse_solve_kernel<TI, TO><<<dim3(blocks, nseg), 32 * kCoarseRows, 0, s>>>(
-      L.coarse_inv, L.free_rows, n, r, z, nrhs, L.coarse_partial);
+  coarse_solve_kernel<TI, TO><<<dim3(blocks, nseg), 32 * kCoarseWarps, 0, s>>>(
+      L.coarse_inv, L.free_rows, n, r, z, nrhs, npad, L.coarse_partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nseg == 1) return e;
   coarse_sum_kernel<TO><<<(n * nrhs + 255) / 256, 256, 0, s>>>(L.coarse_partial, L.free_rows, n,

@@ -11,6 +11,24 @@
 namespace nnmg {
 namespace {
 
+// FP32 -> FP64 widening on the integer pipes.  The conversion instruction runs
+// on GB300's FP64 pipe (2 operations per clock per SM, shared with the FMAs of
+// the FP64 dot products and updates), so kernels that widen every element
+// re-pack the IEEE-754 fields instead: a normal float's exponent is rebiased
+// (127 -> 1023) and its 23 fraction bits move to the top of the 52, which is
+// exact.  Zeros keep their sign; subnormals, infinities and NaNs (not produced
+// by the solver) take the conversion instruction.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)sign);
+  if (ex == 0 || ex == 0xffu) return (double)f;
+  return __longlong_as_double(
+      (long long)(sign | ((uint64_t)(ex + 896u) << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 inline unsigned vblocks(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
@@ -96,16 +114,28 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const double* __restri
   const unsigned act = dot_threads(nrhs);
   const unsigned n = (unsigned)(rows * nrhs);
   double v = 0.0;
-  if (threadIdx.x < act)
-    for (unsigned e = blockIdx.x * act + threadIdx.x; e < n; e += gridDim.x * act)
-      v += a[e] * (double)b[e];
+  if (threadIdx.x < act) {
+    // four independent chains keep eight loads in flight per thread; the
+    // order of the additions is still fixed
+    const unsigned st = gridDim.x * act;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    unsigned e = blockIdx.x * act + threadIdx.x;
+    for (; (uint64_t)e + 3ull * st < n; e += 4 * st) {
+      v0 += a[e] * widen(b[e]);
+      v1 += a[e + st] * widen(b[e + st]);
+      v2 += a[e + 2 * st] * widen(b[e + 2 * st]);
+      v3 += a[e + 3 * st] * widen(b[e + 3 * st]);
+    }
+    for (; e < n; e += st) v0 += a[e] * widen(b[e]);
+    v = (v0 + v1) + (v2 + v3);
+  }
   block_store_partials(v, nrhs, partial);
 }
 
 __global__ void __launch_bounds__(kDotThreads) pcg_init_kernel(
     const double* __restrict__ b, const uint8_t* __restrict__ row_free, double* __restrict__ r,
-    double* __restrict__ x, double* __restrict__ p, double* __restrict__ partial, int64_t rows,
-    int nrhs) {
+    float* __restrict__ r32, double* __restrict__ x, double* __restrict__ p,
+    double* __restrict__ partial, int64_t rows, int nrhs) {
   const unsigned act = dot_threads(nrhs);
   const unsigned n = (unsigned)(rows * nrhs);
   double v = 0.0;
@@ -113,6 +143,7 @@ __global__ void __launch_bounds__(kDotThreads) pcg_init_kernel(
     for (unsigned e = blockIdx.x * act + threadIdx.x; e < n; e += gridDim.x * act) {
       const double bv = row_free[e / (unsigned)nrhs] ? b[e] : 0.0;
       r[e] = bv;
+      r32[e] = (float)bv;
       x[e] = 0.0;
       p[e] = 0.0;
       v += bv * bv;
@@ -124,8 +155,11 @@ __global__ void __launch_bounds__(kDotThreads) pcg_init_kernel(
 // lane, lane+32, ...; then a fixed butterfly).  Every lane returns the total.
 __device__ __forceinline__ double sum_partials_warp(const double* partial, int q) {
   const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int bk = lane; bk < kDotBlocks; bk += 32) s += partial[bk * kMaxRhs + q];
+  static_assert(kDotBlocks % 32 == 0, "every lane reads the same number of partials");
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};      // four independent chains
+#pragma unroll
+  for (int i = 0; i < kDotBlocks / 32; ++i) acc[i % 4] += partial[(lane + 32 * i) * kMaxRhs + q];
+  double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
@@ -180,14 +214,15 @@ __global__ void batch_reset_kernel(PcgScalars* sc, double rtol, int maxit) {
 // partial sums of ||b||^2 for batch_admit_scalar_kernel.
 __global__ void __launch_bounds__(kDotThreads) batch_admit_kernel(
     const double* __restrict__ b, const uint8_t* __restrict__ row_free, double* __restrict__ r,
-    double* __restrict__ x, double* __restrict__ p, double* __restrict__ partial, int64_t rows,
-    int nslots, int slot) {
+    float* __restrict__ r32, double* __restrict__ x, double* __restrict__ p,
+    double* __restrict__ partial, int64_t rows, int nslots, int slot) {
   double v = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double bv = row_free[i] ? b[i] : 0.0;
     const int64_t e = i * nslots + slot;
     r[e] = bv;
+    r32[e] = (float)bv;
     x[e] = 0.0;
     p[e] = 0.0;
     v += bv * bv;
@@ -224,20 +259,28 @@ __global__ void pcg_beta_kernel(PcgScalars* sc, const double* partial, int nrhs)
 }
 
 template <typename TZ>
-__global__ void pcg_p_kernel(const PcgScalars* __restrict__ sc, const TZ* __restrict__ z,
-                             double* __restrict__ p, int64_t n, int nrhs) {
-  __shared__ double beta[kMaxRhs];
-  __shared__ int act[kMaxRhs];
-  if (threadIdx.x < kMaxRhs) {
-    beta[threadIdx.x] = sc->beta[threadIdx.x];
-    act[threadIdx.x] = sc->active[threadIdx.x];
+__global__ void __launch_bounds__(kDotThreads) pcg_p_kernel(const PcgScalars* __restrict__ sc,
+                                                            const TZ* __restrict__ z,
+                                                            double* __restrict__ p, int64_t n,
+                                                            int nrhs) {
+  // the dot-product layout: this thread's elements all lie in column t % nrhs
+  const unsigned act = dot_threads(nrhs);
+  if (threadIdx.x >= act) return;
+  const unsigned q = threadIdx.x % (unsigned)nrhs;
+  if (!sc->active[q]) return;
+  const double beta = sc->beta[q];
+  const unsigned un = (unsigned)n, st = gridDim.x * act;
+  unsigned e = blockIdx.x * act + threadIdx.x;
+  for (; (uint64_t)e + 3ull * st < un; e += 4 * st) {
+    const double z0 = widen(z[e]), z1 = widen(z[e + st]), z2 = widen(z[e + 2 * st]),
+                 z3 = widen(z[e + 3 * st]);
+    const double p0 = p[e], p1 = p[e + st], p2 = p[e + 2 * st], p3 = p[e + 3 * st];
+    p[e] = z0 + beta * p0;
+    p[e + st] = z1 + beta * p1;
+    p[e + 2 * st] = z2 + beta * p2;
+    p[e + 3 * st] = z3 + beta * p3;
   }
-  __syncthreads();
-  const unsigned un = (unsigned)n, ur = (unsigned)nrhs;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < un; e += gridDim.x * blockDim.x) {
-    const unsigned q = e % ur;
-    if (act[q]) p[e] = (double)z[e] + beta[q] * p[e];
-  }
+  for (; e < un; e += st) p[e] = widen(z[e]) + beta * p[e];
 }
 
 // alpha = rho / (p.q); breakdown if p.q <= 0 or non-finite on an active column
@@ -266,8 +309,8 @@ __global__ void pcg_alpha_kernel(PcgScalars* sc, const double* partial, int nrhs
 // x += alpha p; r -= alpha q; q = 0; partial ||r||^2
 __global__ void __launch_bounds__(kDotThreads) pcg_update_kernel(
     const PcgScalars* __restrict__ sc, const double* __restrict__ p, double* __restrict__ qv,
-    double* __restrict__ x, double* __restrict__ r, double* __restrict__ partial, int64_t rows,
-    int nrhs) {
+    double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32,
+    double* __restrict__ partial, int64_t rows, int nrhs) {
   const unsigned act = dot_threads(nrhs);
   const unsigned n = (unsigned)(rows * nrhs);
   double v = 0.0;
@@ -278,11 +321,28 @@ __global__ void __launch_bounds__(kDotThreads) pcg_update_kernel(
       const double rr = re - al * qq;
       x[e] = xe + al * pe;
       r[e] = rr;
+      r32[e] = (float)rr;
       qv[e] = 0.0;
       v += rr * rr;
     }
   }
   block_store_partials(v, nrhs, partial);
+}
+
+// Device-side PCG loop (a CUDA graph WHILE node around one captured
+// iteration): the first kernel arms the loop if any column is active, the
+// last kernel of every iteration re-arms it while a column is active and
+// fewer than maxit iterations ran, so the loop always ends.
+__global__ void pcg_loop_begin_kernel(cudaGraphConditionalHandle hc, const PcgScalars* sc,
+                                      int* count) {
+  *count = 0;
+  cudaGraphSetConditional(hc, sc->any_active ? 1u : 0u);
+}
+__global__ void pcg_loop_next_kernel(cudaGraphConditionalHandle hc, const PcgScalars* sc,
+                                     int* count) {
+  const int c = *count + 1;
+  *count = c;
+  cudaGraphSetConditional(hc, (sc->any_active && c < sc->maxit) ? 1u : 0u);
 }
 
 __global__ void pcg_check_kernel(PcgScalars* sc, const double* partial, int nrhs) {
@@ -403,10 +463,12 @@ cudaError_t launch_dot_partial(const double* a, const TB* b, double* partial, in
   dot_kernel<TB><<<kDotBlocks, kDotThreads, 0, s>>>(a, b, partial, rows, nrhs);
   return cudaGetLastError();
 }
-cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r, double* x,
-                            double* p, double* partial, int64_t rows, int nrhs, cudaStream_t s) {
+cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r, float* r32,
+                            double* x, double* p, double* partial, int64_t rows, int nrhs,
+                            cudaStream_t s) {
   if (too_big(rows * nrhs)) return cudaErrorInvalidValue;
-  pcg_init_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, row_free, r, x, p, partial, rows, nrhs);
+  pcg_init_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, row_free, r, r32, x, p, partial, rows,
+                                                     nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_start(PcgScalars* sc, const double* partial, int nrhs, double rtol,
@@ -418,10 +480,10 @@ cudaError_t launch_batch_reset(PcgScalars* sc, double rtol, int maxit, cudaStrea
   batch_reset_kernel<<<1, 32, 0, s>>>(sc, rtol, maxit);
   return cudaGetLastError();
 }
-cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double* r, double* x,
-                               double* p, double* partial, PcgScalars* sc, int64_t rows,
-                               int nslots, int slot, cudaStream_t s) {
-  batch_admit_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, row_free, r, x, p, partial, rows,
+cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double* r, float* r32,
+                               double* x, double* p, double* partial, PcgScalars* sc,
+                               int64_t rows, int nslots, int slot, cudaStream_t s) {
+  batch_admit_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, row_free, r, r32, x, p, partial, rows,
                                                        nslots, slot);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -436,7 +498,7 @@ cudaError_t launch_pcg_beta_p(PcgScalars* sc, const double* partial, const TZ* z
   if (e != cudaSuccess) return e;
   const int64_t n = rows * nrhs;
   if (too_big(n)) return cudaErrorInvalidValue;
-  pcg_p_kernel<TZ><<<vblocks(n), 256, 0, s>>>(sc, z, p, n, nrhs);
+  pcg_p_kernel<TZ><<<kDotBlocks, kDotThreads, 0, s>>>(sc, z, p, n, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_alpha(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s) {
@@ -444,9 +506,20 @@ cudaError_t launch_pcg_alpha(PcgScalars* sc, const double* partial, int nrhs, cu
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_update(const PcgScalars* sc, const double* p, double* q, double* x,
-                              double* r, double* partial, int64_t rows, int nrhs, cudaStream_t s) {
+                              double* r, float* r32, double* partial, int64_t rows, int nrhs,
+                              cudaStream_t s) {
   if (too_big(rows * nrhs)) return cudaErrorInvalidValue;
-  pcg_update_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(sc, p, q, x, r, partial, rows, nrhs);
+  pcg_update_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(sc, p, q, x, r, r32, partial, rows, nrhs);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_loop_begin(cudaGraphConditionalHandle hc, const PcgScalars* sc, int* count,
+                                  cudaStream_t s) {
+  pcg_loop_begin_kernel<<<1, 1, 0, s>>>(hc, sc, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_loop_next(cudaGraphConditionalHandle hc, const PcgScalars* sc, int* count,
+                                 cudaStream_t s) {
+  pcg_loop_next_kernel<<<1, 1, 0, s>>>(hc, sc, count);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s) {

@@ -203,23 +203,31 @@ constexpr int kDotThreads = 256;
 template <typename TB>
 cudaError_t launch_dot_partial(const double* a, const TB* b, double* partial, int64_t rows,
                                int nrhs, cudaStream_t s);
-cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r, double* x,
-                            double* p, double* partial, int64_t rows, int nrhs, cudaStream_t s);
+// The PCG writers of r also write r32 = (float) r, the FP32 V-cycle's input.
+cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r, float* r32,
+                            double* x, double* p, double* partial, int64_t rows, int nrhs,
+                            cudaStream_t s);
 cudaError_t launch_pcg_start(PcgScalars* sc, const double* partial, int nrhs, double rtol,
                              int maxit, cudaStream_t s);
 // Continuous batching: reset every column to inactive; start column `slot`
 // from the right-hand side b [rows] (r = b on free rows, x = p = 0).
 cudaError_t launch_batch_reset(PcgScalars* sc, double rtol, int maxit, cudaStream_t s);
-cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double* r, double* x,
-                               double* p, double* partial, PcgScalars* sc, int64_t rows,
-                               int nslots, int slot, cudaStream_t s);
+cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double* r, float* r32,
+                               double* x, double* p, double* partial, PcgScalars* sc,
+                               int64_t rows, int nslots, int slot, cudaStream_t s);
 template <typename TZ>
 cudaError_t launch_pcg_beta_p(PcgScalars* sc, const double* partial, const TZ* z, double* p,
                               int64_t rows, int nrhs, cudaStream_t s);
 cudaError_t launch_pcg_alpha(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s);
 cudaError_t launch_pcg_update(const PcgScalars* sc, const double* p, double* q, double* x,
-                              double* r, double* partial, int64_t rows, int nrhs, cudaStream_t s);
+                              double* r, float* r32, double* partial, int64_t rows, int nrhs,
+                              cudaStream_t s);
 cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s);
+// Loop control of the device-side PCG loop (graph conditional WHILE node).
+cudaError_t launch_pcg_loop_begin(cudaGraphConditionalHandle hc, const PcgScalars* sc, int* count,
+                                  cudaStream_t s);
+cudaError_t launch_pcg_loop_next(cudaGraphConditionalHandle hc, const PcgScalars* sc, int* count,
+                                 cudaStream_t s);
 // Lanczos helper: w = dinv .* u - beta * vprev  (nrhs = 1)
 cudaError_t launch_axpby_dinv(const double* u, const double* dinv, const double* vprev,
                               double beta, double* w, int64_t rows, cudaStream_t s);

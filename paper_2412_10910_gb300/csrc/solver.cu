@@ -39,11 +39,15 @@ struct nnmg_handle {
   WorkSet<double> w64;
   bool pcg_ready = false;
   double *px = nullptr, *pr = nullptr, *pp = nullptr, *pq = nullptr, *pb = nullptr;
+  float* pr32 = nullptr;   // (float) pr: the FP32 V-cycle's input, written with pr
   double* partial = nullptr;
   PcgScalars* sc = nullptr;
   PcgScalars* h_sc = nullptr;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (kind, prec/mode, nrhs)
   std::map<std::tuple<int, int, int>, int> runs;
+  // device-side PCG loops per (mode, nrhs); nullptr marks a failed build
+  std::map<std::tuple<int, int>, cudaGraphExec_t> loops;
+  int* loop_count = nullptr;
   std::map<std::tuple<int, int, int>, int> op_units;  // (level, precision, nrhs) -> units
   // wall seconds of the setup phases (see nnmg_setup_seconds in nnmg.h)
   double setup_s[NNMG_SETUP_PHASES] = {0};
@@ -149,9 +153,11 @@ int ensure_pcg(nnmg_handle* h) {
   CK(dalloc(h, &h->pp, m, true));
   CK(dalloc(h, &h->pq, m, true));
   CK(dalloc(h, &h->pb, m, true));
+  CK(dalloc(h, &h->pr32, m, true));
   CK(cudaMemset(h->pq, 0, m * sizeof(double)));
   CK(dalloc(h, &h->partial, (size_t)kDotBlocks * kMaxRhs, true));
   CK(dalloc(h, &h->sc, 1, true));
+  CK(dalloc(h, &h->loop_count, 1, true));
   CK(cudaMallocHost((void**)&h->h_sc, sizeof(PcgScalars)));
   h->pcg_ready = true;
   return NNMG_OK;
@@ -307,9 +313,7 @@ cudaError_t enqueue_pcg_iter(nnmg_handle* h, int mode, int nrhs, cudaStream_t s)
   const int64_t rows = L.rows;
   cudaError_t e;
   if (mode == NNMG_FP32_MG_FP64_CG || mode == NNMG_FP32_MG_DW_CG) {
-    e = launch_cast<double, float>(h->pr, h->w32.f[top], rows * nrhs, s);
-    if (e != cudaSuccess) return e;
-    e = enqueue_vcycle<float>(h, h->w32.f[top], nrhs, s);
+    e = enqueue_vcycle<float>(h, h->pr32, nrhs, s);
     if (e != cudaSuccess) return e;
     const float* z = h->w32.x[top];
     if ((e = launch_dot_partial<float>(h->pr, z, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
@@ -330,7 +334,7 @@ cudaError_t enqueue_pcg_iter(nnmg_handle* h, int mode, int nrhs, cudaStream_t s)
   if (e != cudaSuccess) return e;
   if ((e = launch_dot_partial<double>(h->pp, h->pq, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
   if ((e = launch_pcg_alpha(h->sc, h->partial, nrhs, s)) != cudaSuccess) return e;
-  if ((e = launch_pcg_update(h->sc, h->pp, h->pq, h->px, h->pr, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
+  if ((e = launch_pcg_update(h->sc, h->pp, h->pq, h->px, h->pr, h->pr32, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
   return launch_pcg_check(h->sc, h->partial, nrhs, s);
 }
 
@@ -369,6 +373,61 @@ int run_graph(nnmg_handle* h, std::tuple<int, int, int> key, cudaStream_t s, F b
   h->graphs[key] = ex;
   CK(cudaGraphLaunch(ex, s));
   return NNMG_OK;
+}
+
+// The whole PCG loop as one graph: a kernel arms a WHILE node whose body is
+// one iteration (the kernels of enqueue_pcg_iter) and the re-arming kernel;
+// the host then waits once per solve instead of once per iteration.  Built
+// after the iteration has run eagerly (so the autotuner's choices exist);
+// returns nullptr if the graph cannot be built (the host-driven loop runs).
+cudaGraphExec_t build_pcg_loop(nnmg_handle* h, int mode, int nrhs) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaGraphConditionalHandle hc;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&hc, g, 0, 0) == cudaSuccess;
+  cudaGraphNode_t pre = nullptr;
+  if (ok) {
+    ok = cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const bool launched = launch_pcg_loop_begin(hc, h->sc, h->loop_count, h->cap) == cudaSuccess;
+      cudaGraph_t gg = g;
+      ok = cudaStreamEndCapture(h->cap, &gg) == cudaSuccess && launched;
+    }
+    size_t nn = 0;
+    ok = ok && cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn == 1 &&
+         cudaGraphGetNodes(g, &pre, &nn) == cudaSuccess;
+  }
+  cudaGraph_t body = nullptr;
+  if (ok) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    ok = cudaGraphAddNode(&cn, g, &pre, nullptr, 1, &cp) == cudaSuccess;
+    if (ok) body = cp.conditional.phGraph_out[0];
+  }
+  if (ok) {
+    ok = cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      bool launched = enqueue_pcg_iter(h, mode, nrhs, h->cap) == cudaSuccess;
+      launched = launched && launch_pcg_loop_next(hc, h->sc, h->loop_count, h->cap) == cudaSuccess;
+      cudaGraph_t bb = body;
+      ok = cudaStreamEndCapture(h->cap, &bb) == cudaSuccess && launched;
+    }
+  }
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    if (ex) cudaGraphExecDestroy(ex);
+    ex = nullptr;
+    cudaGetLastError();   // leave no sticky error behind
+  }
+  return ex;
 }
 
 // ------------------------------------------------------------------ setup
@@ -712,6 +771,8 @@ int check_vec_args(nnmg_handle* h, int level, int precision, int nrhs, bool allo
 
 void destroy_impl(nnmg_handle* h) {
   if (h->batch_ev) cudaEventDestroy(h->batch_ev);
+  for (auto& kv : h->loops)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -852,7 +913,7 @@ size_t nnmg_solve_bytes(const nnmg_handle* h, int nrhs) {
     if (l) per += (size_t)h->lv[l - 1].n_cells * h->lv[l - 1].nloc * L.ncomp * nrhs;
     b += per * (sizeof(float) + sizeof(double));
   }
-  b += (size_t)h->lv.back().rows * nrhs * 5 * sizeof(double);
+  b += (size_t)h->lv.back().rows * nrhs * (5 * sizeof(double) + sizeof(float));
   return b;
 }
 
@@ -910,6 +971,16 @@ int nnmg_transfer_points(const nnmg_handle* h, int fine_level, int32_t* cell, do
   const DevLevel& F = h->lv[fine_level];
   if (cell) std::memcpy(cell, F.h_loc_cell.data(), F.h_loc_cell.size() * sizeof(int32_t));
   if (xi) std::memcpy(xi, F.h_loc_xi.data(), F.h_loc_xi.size() * sizeof(double));
+  return NNMG_OK;
+}
+
+int nnmg_pcg_device_loop(const nnmg_handle* h, int mode, int nrhs, int* state) {
+  if (!h || !state) {
+    set_error("nnmg_pcg_device_loop: null handle or pointer");
+    return NNMG_INVALID_ARG;
+  }
+  auto it = h->loops.find(std::make_tuple(mode, nrhs));
+  *state = it == h->loops.end() ? 0 : (it->second ? 1 : -1);
   return NNMG_OK;
 }
 
@@ -1080,6 +1151,9 @@ int nnmg_set_nested(nnmg_handle* h, int fine_level, const int32_t* parent_cell,
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);   // the V-cycle changes
   h->graphs.clear();
   h->runs.clear();
+  for (auto& kv : h->loops)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  h->loops.clear();
   if (!parent_cell) {
     F.gc_active = false;
     return NNMG_OK;
@@ -1126,6 +1200,7 @@ int nnmg_batch_reset(nnmg_handle* h, int mode, int nslots, double rtol, int maxi
   const size_t n = (size_t)h->lv.back().rows * nslots * sizeof(double);
   NNMG_CUDA(cudaMemsetAsync(h->px, 0, n, s));
   NNMG_CUDA(cudaMemsetAsync(h->pr, 0, n, s));
+  NNMG_CUDA(cudaMemsetAsync(h->pr32, 0, n / 2, s));
   NNMG_CUDA(cudaMemsetAsync(h->pp, 0, n, s));
   NNMG_CUDA(cudaMemsetAsync(h->pq, 0, n, s));
   NNMG_CUDA(launch_batch_reset(h->sc, rtol, maxit, s));
@@ -1147,8 +1222,8 @@ int nnmg_batch_admit(nnmg_handle* h, int slot, const double* b, int b_on_host, v
     NNMG_CUDA(cudaMemcpyAsync(h->pb, b, (size_t)L.rows * sizeof(double), cudaMemcpyHostToDevice, s));
     src = h->pb;
   }
-  NNMG_CUDA(launch_batch_admit(src, L.row_free, h->pr, h->px, h->pp, h->partial, h->sc, L.rows,
-                               h->batch_slots, slot, s));
+  NNMG_CUDA(launch_batch_admit(src, L.row_free, h->pr, h->pr32, h->px, h->pp, h->partial, h->sc,
+                               L.rows, h->batch_slots, slot, s));
   return NNMG_OK;
 }
 
@@ -1215,6 +1290,8 @@ int nnmg_batch_retire(nnmg_handle* h, int slot, double* x, int x_on_host, void* 
 }  // extern "C"
 
 namespace {
+int pcg_result(nnmg_handle* h, int nrhs, double rtol, int* iters_out, double* relres_out);
+
 // PCG from x0 = 0 on device right-hand sides b; the solution stays in h->px.
 int pcg_run(nnmg_handle* h, int mode, const double* b, int nrhs, double rtol, int maxit,
             int* iters_out, double* relres_out, cudaStream_t s) {
@@ -1223,8 +1300,22 @@ int pcg_run(nnmg_handle* h, int mode, const double* b, int nrhs, double rtol, in
   if ((rc = (mode == NNMG_FP64_MG ? ensure_work<double>(h) : ensure_work<float>(h)))) return rc;
   if (mode == NNMG_FP32_MG_DW_CG && (rc = ensure_dw(h, (int)h->lv.size() - 1))) return rc;
   const DevLevel& L = h->lv.back();
-  NNMG_CUDA(launch_pcg_init(b, L.row_free, h->pr, h->px, h->pp, h->partial, L.rows, nrhs, s));
+  NNMG_CUDA(launch_pcg_init(b, L.row_free, h->pr, h->pr32, h->px, h->pp, h->partial, L.rows, nrhs, s));
   NNMG_CUDA(launch_pcg_start(h->sc, h->partial, nrhs, rtol, maxit, s));
+  // device-side loop once the single-iteration graph exists (NNMG_DEVICE_LOOP=0
+  // keeps the host-driven loop)
+  const char* dl = getenv("NNMG_DEVICE_LOOP");
+  const auto lkey = std::make_tuple(mode, nrhs);
+  if (!(dl && dl[0] == '0') && h->graphs.count(std::make_tuple(1, mode, nrhs))) {
+    auto it = h->loops.find(lkey);
+    if (it == h->loops.end()) it = h->loops.emplace(lkey, build_pcg_loop(h, mode, nrhs)).first;
+    if (it->second) {
+      NNMG_CUDA(cudaGraphLaunch(it->second, s));
+      NNMG_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+      NNMG_CUDA(cudaStreamSynchronize(s));
+      return pcg_result(h, nrhs, rtol, iters_out, relres_out);
+    }
+  }
   NNMG_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   NNMG_CUDA(cudaStreamSynchronize(s));
   bool active = h->h_sc->any_active != 0;
@@ -1237,6 +1328,11 @@ int pcg_run(nnmg_handle* h, int mode, const double* b, int nrhs, double rtol, in
     NNMG_CUDA(cudaStreamSynchronize(s));
     active = h->h_sc->any_active != 0;
   }
+  return pcg_result(h, nrhs, rtol, iters_out, relres_out);
+}
+
+// Per-column results of the finished PCG (host copy of the scalars).
+int pcg_result(nnmg_handle* h, int nrhs, double rtol, int* iters_out, double* relres_out) {
   const PcgScalars& sc = *h->h_sc;
   bool conv = true;
   for (int q = 0; q < nrhs; ++q) {

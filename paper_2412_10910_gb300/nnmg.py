@@ -151,6 +151,12 @@ def nnmg_transfer_points(h, fine_level, dim):
     return cell, xi
 
 
+def nnmg_pcg_device_loop(h, mode, nrhs):
+    out = C.c_int(0)
+    _check(_lib.nnmg_pcg_device_loop(h, mode, nrhs, C.byref(out)), "nnmg_pcg_device_loop")
+    return out.value
+
+
 SETUP_PHASES = ("numbering", "level_geometry", "point_location", "gather_lists", "lanczos",
                 "coarse_inverse")
 
@@ -346,6 +352,11 @@ class Hierarchy:
 
     def eigen_estimates(self):
         return nnmg_eigen_estimates(self.h)
+
+    def pcg_device_loop(self, mode, nrhs):
+        """1: solves for (mode, nrhs) run as one device-side graph loop; 0: not
+        built yet; -1: could not be built (host-driven loop)."""
+        return nnmg_pcg_device_loop(self.h, mode, nrhs)
 
     def setup_seconds(self):
         """Wall seconds of the setup phases, by name."""

@@ -18,6 +18,9 @@ CASES = {
     "c2_q2_3lev": (lambda: config_levels("c2_3d_q2", n_levels=3), 2, 1, (1.0, 1.0), 3, 8),
     "c3_q4_2lev": (lambda: config_levels("c3_3d_q4_deformed", n_levels=2), 4, 1, (1.0, 1.0), 5, 4),
     "c4_elast": (lambda: config_levels("c4_3d_q2_elasticity"), 2, 3, (10.0, 1.0), 4, 1),
+    # the largest channel count: 3 components x 16 right-hand sides
+    "c4_elast_16rhs": (lambda: config_levels("c4_3d_q2_elasticity", n_levels=2), 2, 3, (10.0, 1.0),
+                       4, 16),
     "scrambled_q3": (lambda: [scramble(box_level((2, 2, 2), alpha=0.1, seed=3), 5),
                               scramble(box_level((5, 4, 3), alpha=0.2, seed=4), 6)], 3, 1,
                      (1.0, 1.0), 3, 2),
