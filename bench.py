@@ -505,7 +505,11 @@ def main():
         torch.cuda.nvtx.range_pop()
         barrier()
         if rank == 0:
-            print(json.dumps({"only": args.only, "ms_per_step": e0.elapsed_time(e1) / args.steps}))
+            choice = {p: H.operator_choice(top, p, nrhs) for p in (_abi.F32, _abi.F64, _abi.F64_DW)}
+            print(json.dumps({"only": args.only, "config": name,
+                              "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                              "operator_choice_top": {"f32": choice[_abi.F32], "f64": choice[_abi.F64],
+                                                      "f64_dw": choice[_abi.F64_DW]}}))
         H.close()
         return
 

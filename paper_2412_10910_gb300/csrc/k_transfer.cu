@@ -102,6 +102,10 @@ __global__ void prolong_kernel(const int32_t* __restrict__ coarse_cell_nodes,
   }
 }
 
+// Phase one: thread (m_0[, m_1], channel) owns the N buffer entries that
+// differ in the last local index; per fine point it forms
+// phi_{m_0}(xi_0) [phi_{m_1}(xi_1)] r_p once and adds it times each of the
+// last direction's N basis values (points in stored order: deterministic).
 template <int D, int K, typename T>
 __global__ void restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
                                  const int32_t* __restrict__ cell_pt_start,
@@ -109,17 +113,20 @@ __global__ void restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
                                  int nch, Basis1D<T> B) {
   constexpr int N = K + 1;
   constexpr int NL = D == 2 ? N * N : N * N * N;
+  constexpr int NP = NL / N;                   // (m_0[, m_1]) combinations
   __shared__ T sL[kChunk][D][N];
   extern __shared__ unsigned char smem_raw[];
   T* sr = reinterpret_cast<T*>(smem_raw);  // [kChunk][nch]
   const int64_t c = blockIdx.x;
   const int e = blockIdx.y * blockDim.x + threadIdx.x;
-  const bool valid = e < NL * nch;
-  const int j = valid ? e / nch : 0;
-  const int ch = valid ? e - j * nch : 0;
-  const int mi[3] = {j % N, (j / N) % N, j / (N * N)};
+  const bool valid = e < NP * nch;
+  const int jp = valid ? e / nch : 0;
+  const int ch = valid ? e - jp * nch : 0;
+  const int m0 = jp % N, m1 = jp / N;          // m1 unused in 2D
   const int p0 = cell_pt_start[c], p1 = cell_pt_start[c + 1];
-  T acc = 0;
+  T acc[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) acc[m] = 0;
   for (int q0 = p0; q0 < p1; q0 += kChunk) {
     const int np = min(kChunk, p1 - q0);
     for (int t = threadIdx.x; t < np * D; t += blockDim.x) {
@@ -133,14 +140,18 @@ __global__ void restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
     __syncthreads();
     if (valid) {
       for (int pp = 0; pp < np; ++pp) {
-        T w = sL[pp][0][mi[0]] * sL[pp][1][mi[1]];
-        if constexpr (D == 3) w *= sL[pp][2][mi[2]];
-        acc += w * sr[pp * nch + ch];
+        T w = sL[pp][0][m0] * sr[pp * nch + ch];
+        if constexpr (D == 3) w *= sL[pp][1][m1];
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc[m] += w * sL[pp][D - 1][m];
       }
     }
     __syncthreads();
   }
-  if (valid) buf[(c * NL + j) * nch + ch] = acc;
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < N; ++m) buf[(c * NL + jp + NP * m) * nch + ch] = acc[m];
+  }
 }
 
 template <typename T>
@@ -286,8 +297,8 @@ cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* rc
   static size_t granted = 0;
   cudaError_t e = allow_smem(kern, smem, &granted);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)c.n_cells, (unsigned)((NL * nch + 255) / 256));
-  kern<<<grid, 256, smem, s>>>(rf, scratch, f.cell_pt_start, f.pt_node, xi_of<T>(f), nch, B);
+  dim3 grid((unsigned)c.n_cells, (unsigned)((NL / N * nch + 127) / 128));
+  kern<<<grid, 128, smem, s>>>(rf, scratch, f.cell_pt_start, f.pt_node, xi_of<T>(f), nch, B);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = c.n_nodes * nch;
