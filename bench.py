@@ -65,6 +65,79 @@ def poisson3d_work(n):
     return flops, ops
 
 
+def fine_level_kernel_bytes(dim, k, kc, ncomp, nrhs, s, cheb, fine, coarse):
+    """Algorithmic DRAM bytes of the fine level's V-cycle kernels, per launch
+    (operator, restriction, prolongation) or per V-cycle (vector kernels).
+
+    fine / coarse: (n_nodes, n_free, n_cells) of the two levels; k, kc their
+    degrees; s the value size.  Vectors are [rows][ncomp * nrhs].
+    operator: read x and write y at free rows, plus per cell the metric terms
+      (6 (3D) / 3 (2D) Poisson, 9 elasticity, s bytes each) and the node
+      indices (4 B) of its (k+1)^d quadrature points / nodes.
+    vector kernels of one V-cycle: Chebyshev start (read f, write d, x), 2m-1
+      Chebyshev steps (read f, t, d, x; write d, x, t), the residual (read f,
+      t; write r, t), plus the Jacobi diagonal per row in each of the 2m+1.
+    restriction: read the fine residual at the located points with their node
+      index (4 B) and reference point (d s B), write the coarse vector, and
+      the cell-local buffer of the deterministic two-phase gather (written,
+      read back) with its gather list (4 B per cell-local entry).
+    prolongation: read the coarse vector once and the coarse cells' node
+      indices, read and write the fine vector at the located points with
+      their node index and reference point."""
+    nn_f, nf_f, nc_f = fine
+    nn_c, nf_c, nc_c = coarse
+    ch = ncomp * nrhs
+    nloc, nloc_c = (k + 1) ** dim, (kc + 1) ** dim
+    nmetric = 9 if ncomp == 3 else (6 if dim == 3 else 3)
+    rows_f = nn_f * ncomp
+    op = 2 * nf_f * ch * s + nc_f * nloc * (nmetric * s + 4)
+    vec = rows_f * nrhs * s * (3 + (2 * cheb - 1) * 7 + 4) + (2 * cheb + 1) * rows_f * s
+    n_pts = nf_f
+    pts = n_pts * (4 + dim * s)
+    buf = nc_c * nloc_c * ch * s
+    restrict = n_pts * ch * s + pts + nn_c * ch * s + 2 * buf + nc_c * nloc_c * 4
+    prolong = nn_c * ch * s + nc_c * nloc_c * 4 + 2 * n_pts * ch * s + pts
+    return {"operator": op, "vector": vec, "restrictor": restrict, "prolongator": prolong}
+
+
+def vcycle_kernel_table(H, degrees, ncomp, nrhs, cheb, hbm_gbs, reps=5):
+    """Per-level V-cycle breakdown (paper Sec. 5 components) in FP32 and the
+    achieved HBM bandwidth of the fine level's kernels, from the library's
+    event-timed profile run (nnmg_vcycle_profile)."""
+    import numpy as np
+    import torch
+    from paper_2412_10910_gb300 import _abi
+    top = H.n_levels - 1
+    r = torch.randn(H.rows(top), nrhs, dtype=torch.float32, device="cuda")
+    r[torch.tensor(np.repeat(H.constrained(top), ncomp), device="cuda")] = 0
+    z = torch.empty_like(r)
+    H.vcycle_profile(r, z)                        # warm-up
+    acc, cnt = None, None
+    for _ in range(reps):
+        ms, cnt = H.vcycle_profile(r, z)
+        acc = ms if acc is None else acc + ms
+    ms = acc / reps
+    cols = _abi.PROF_COLUMNS
+    breakdown = {f"level{lv}": {c: round(float(ms[lv, i]), 4) for i, c in enumerate(cols[:6])
+                                if cnt[lv, i] > 0}
+                 for lv in range(H.n_levels)}
+    dim = H.dim
+    fine, coarse = H.info(top), H.info(top - 1)
+    by = fine_level_kernel_bytes(dim, degrees[top], degrees[top - 1], ncomp, nrhs, 4, cheb,
+                                 fine, coarse)
+    col = {c: i for i, c in enumerate(cols)}
+    kern = {}
+    for name, per_launch in (("operator", True), ("vector", False), ("restrictor", True),
+                             ("prolongator", True)):
+        n = int(cnt[top, col[name]]) if per_launch else 1
+        t_ms = float(ms[top, col[name]]) / max(n, 1)
+        gbs = by[name] / (t_ms / 1e3) / 1e9
+        kern[name] = {"ms_per_launch" if per_launch else "ms_per_vcycle": round(t_ms, 5),
+                      "algorithmic_bytes": int(by[name]), "achieved_gbs": round(gbs, 1),
+                      "frac_of_measured_hbm": round(gbs / hbm_gbs, 3)}
+    return breakdown, kern
+
+
 def operator_kernel_name(choice, k, dtype):
     if choice == -1:
         return f"op_reg_kernel<3,{k},{dtype}> (register-resident)"
@@ -575,6 +648,11 @@ def main():
     top32, _ = timed(lambda: H.apply(top, x32, y32), 10, 3)
     topdw, _ = timed(lambda: H.apply(top, x64, y64, double_word=True), 10, 3)
 
+    # ---- per-level V-cycle breakdown and HBM fraction of the fine level's kernels
+    peaks, peak_kind = _peaks()
+    breakdown, kern_hbm = vcycle_kernel_table(H, [cfg["degree"]] * H.n_levels, 1, nrhs, cfg["cheb"],
+                                              peaks["hbm_gbs"])
+
     # ---- end to end through the host-buffer C call
     bh = torch.empty(rows * nrhs, dtype=torch.float64, pin_memory=True)
     bh.copy_(b.reshape(-1).cpu())
@@ -597,7 +675,6 @@ def main():
     pipe = ops_cell * n_cells * nrhs / (op64_ms / 1e3) / 1e12
     from paper_2412_10910_gb300 import _abi
     choice64 = H.operator_choice(top, _abi.F64, nrhs)
-    peaks, peak_kind = _peaks()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -632,6 +709,10 @@ def main():
                      "traffic": OP64_TRAFFIC.get(choice64),
                      "peak_source": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz "
                                     "(an FMA-chain probe reached 0.596 T/s = 0.95 of it)"},
+        # FP32 V-cycle per level and component (ms, event-timed eager run) and the
+        # fine level's kernels against the measured HBM copy bandwidth
+        "vcycle_breakdown_ms": breakdown,
+        "fine_level_kernels_hbm": kern_hbm,
         "e2e": {"value": dofs * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": rows * nrhs * 8, "d2h_bytes_per_step": rows * nrhs * 8},
         "gpu_launches": kernels_per_solve(H.n_levels, cfg["cheb"], int(max(iters))) * args.steps,

@@ -251,6 +251,32 @@ int nnmg_set_nested(nnmg_handle* h, int fine_level, const int32_t* parent_cell,
 int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
                 void* stream);
 
+/* One V-cycle exactly as nnmg_vcycle (same kernels, same z), run eagerly with
+ * CUDA events around every kernel, to time its parts per level as the paper's
+ * Sec. 5 does (Fig. breakdown_serial: pre-smoother, residual, restrictor,
+ * coarse-grid solver, prolongator, post-smoother).  Waits for `stream`.
+ * ms (host, [n_levels][NNMG_PROF_COLS], overwritten): milliseconds summed
+ * over the launches of each (level, column); columns NNMG_PROF_PRE ..
+ * NNMG_PROF_POST are the six components (the coarse solve on level 0, the
+ * others on levels >= 1; restriction and prolongation are booked on the fine
+ * level of their pair), NNMG_PROF_OPERATOR and NNMG_PROF_VECTOR the same
+ * launches by kernel class (operator applications; Chebyshev and residual
+ * vector updates).  launches (host, same shape, may be NULL): how many
+ * launches each entry sums.  Event timing adds a few microseconds per launch
+ * on small levels.  INVALID_ARG for bad arguments or when called inside a
+ * stream capture. */
+#define NNMG_PROF_PRE 0
+#define NNMG_PROF_RESIDUAL 1
+#define NNMG_PROF_RESTRICT 2
+#define NNMG_PROF_COARSE 3
+#define NNMG_PROF_PROLONG 4
+#define NNMG_PROF_POST 5
+#define NNMG_PROF_OPERATOR 6
+#define NNMG_PROF_VECTOR 7
+#define NNMG_PROF_COLS 8
+int nnmg_vcycle_profile(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
+                        void* stream, double* ms, int* launches);
+
 /* PCG in FP64 from x0 = 0, preconditioned by one V-cycle per iteration
  * (Sec. 4), per column until ||r_k||_2 <= rtol ||b||_2 (recursive residual).
  * b, x: device FP64 [rows][nrhs]; iters_out, relres_out: host [nrhs] (may be

@@ -9,6 +9,9 @@ OK, INVALID_ARG, BAD_MESH, POINT_NOT_FOUND, CHOLESKY_FAIL, OUT_OF_MEMORY, CUDA_E
     NOT_CONVERGED, BREAKDOWN = range(9)
 F32, F64, F64_DW = 0, 1, 2
 FP64_MG, FP32_MG_FP64_CG, FP32_MG_DW_CG = 0, 1, 2
+# columns of nnmg_vcycle_profile
+PROF_COLUMNS = ("pre_smoother", "residual", "restrictor", "coarse_solver", "prolongator",
+                "post_smoother", "operator", "vector")
 
 
 class LevelDesc(C.Structure):
@@ -55,6 +58,8 @@ PROTOTYPES = {
                                         C.c_int, C.c_void_p]),
     "nnmg_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                               C.c_void_p]),
+    "nnmg_vcycle_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "nnmg_pcg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                  C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nnmg_pcg_solve_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,

@@ -246,8 +246,35 @@ int op_units_dw(nnmg_handle* h, int level, int nrhs, cudaStream_t s) {
 // zero guess (m steps, m-1 operator applications), residual, restriction
 // r_{l-1} = P^T r_l, recursion, prolongation x_l += P delta_{l-1},
 // post-smoothing continuing from x_l (m steps), FP64 direct solve on level 0.
+//
+// With a VcycleTimer (nnmg_vcycle_profile) every launch is bracketed by CUDA
+// events and attributed to its level, its component of the paper's Sec. 5
+// breakdown and its kernel class; all other runs pass none.
+struct VcycleTimer {
+  struct Mark {
+    int level, col_component, col_kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  ~VcycleTimer() {
+    for (auto& m : marks) {
+      if (m.a) cudaEventDestroy(m.a);
+      if (m.b) cudaEventDestroy(m.b);
+    }
+  }
+  cudaError_t start(int level, int comp, int kind, cudaStream_t s) {
+    Mark m{level, comp, kind, nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&m.a);
+    if (e == cudaSuccess) e = cudaEventCreate(&m.b);
+    marks.push_back(m);
+    return e == cudaSuccess ? cudaEventRecord(m.a, s) : e;
+  }
+  cudaError_t stop(cudaStream_t s) { return cudaEventRecord(marks.back().b, s); }
+};
+
 template <typename T>
-cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_t s) {
+cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_t s,
+                           VcycleTimer* P = nullptr) {
   WorkSet<T>& W = work_of<T>(h);
   const int top = (int)h->lv.size() - 1;
   const int m = h->opt.cheb_degree;
@@ -258,6 +285,13 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
     e = (__VA_ARGS__);                  \
     if (e != cudaSuccess) return e;     \
   } while (0)
+  // a launch of component `comp` (NNMG_PROF_*) and kernel class `kind`
+#define RUN(level, comp, kind, ...)                   \
+  do {                                                \
+    if (P) RET(P->start(level, comp, kind, s));       \
+    RET(__VA_ARGS__);                                 \
+    if (P) RET(P->stop(s));                           \
+  } while (0)
   for (int l = top; l >= 1; --l) {
     const DevLevel& L = h->lv[l];
     const T* f = l == top ? f_top : W.f[l];
@@ -266,41 +300,52 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
     const int ou = op_units<T>(h, l, nrhs, s);
     const double a = L.cheb_a, b = L.cheb_b;
     const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
-    RET(launch_cheb_init<T>(f, dinv, d, x, 1.0 / theta, L.rows, nrhs, s));
+    RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
+        launch_cheb_init<T>(f, dinv, d, x, 1.0 / theta, L.rows, nrhs, s));
     double rho = 1.0 / sigma;
     for (int j = 1; j < m; ++j) {
-      RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+      RUN(l, NNMG_PROF_PRE, NNMG_PROF_OPERATOR,
+          launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
       const double rn = 1.0 / (2.0 * sigma - rho);
-      RET(launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
+      RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
+          launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
       rho = rn;
     }
-    RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
-    RET(launch_residual<T>(f, t, d, L.rows, nrhs, s));
-    RET(launch_restrict<T>(L, h->lv[l - 1], d, W.f[l - 1], W.scratch[l], nrhs, s));
+    RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_OPERATOR,
+        launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+    RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_VECTOR, launch_residual<T>(f, t, d, L.rows, nrhs, s));
+    RUN(l, NNMG_PROF_RESTRICT, NNMG_PROF_RESTRICT,
+        launch_restrict<T>(L, h->lv[l - 1], d, W.f[l - 1], W.scratch[l], nrhs, s));
   }
   {
     const T* f0 = top == 0 ? f_top : W.f[0];
-    RET(launch_coarse_solve<T, T>(h->lv[0], f0, W.x[0], nrhs, s));
+    RUN(0, NNMG_PROF_COARSE, NNMG_PROF_COARSE,
+        launch_coarse_solve<T, T>(h->lv[0], f0, W.x[0], nrhs, s));
   }
   for (int l = 1; l <= top; ++l) {
     const DevLevel& L = h->lv[l];
     const T* f = l == top ? f_top : W.f[l];
     T *x = W.x[l], *t = W.t[l], *d = W.d[l];
     const T* dinv = dinv_of<T>(L);
-    RET(launch_prolongate_add<T>(L, h->lv[l - 1], W.x[l - 1], x, nrhs, s));
+    RUN(l, NNMG_PROF_PROLONG, NNMG_PROF_PROLONG,
+        launch_prolongate_add<T>(L, h->lv[l - 1], W.x[l - 1], x, nrhs, s));
     const int ou = op_units<T>(h, l, nrhs, s);
     const double a = L.cheb_a, b = L.cheb_b;
     const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
     double rho = 1.0 / sigma;
-    RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
-    RET(launch_cheb_step<T>(f, t, dinv, d, x, 0.0, 1.0 / theta, L.rows, nrhs, s));
+    RUN(l, NNMG_PROF_POST, NNMG_PROF_OPERATOR, launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+    RUN(l, NNMG_PROF_POST, NNMG_PROF_VECTOR,
+        launch_cheb_step<T>(f, t, dinv, d, x, 0.0, 1.0 / theta, L.rows, nrhs, s));
     for (int j = 1; j < m; ++j) {
-      RET(launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+      RUN(l, NNMG_PROF_POST, NNMG_PROF_OPERATOR,
+          launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
       const double rn = 1.0 / (2.0 * sigma - rho);
-      RET(launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
+      RUN(l, NNMG_PROF_POST, NNMG_PROF_VECTOR,
+          launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
       rho = rn;
     }
   }
+#undef RUN
 #undef RET
   return cudaSuccess;
 }
@@ -1135,6 +1180,53 @@ int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
     });
     if (rc) return rc;
     NNMG_CUDA(cudaMemcpyAsync(z, h->w32.x[top], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  return NNMG_OK;
+}
+
+int nnmg_vcycle_profile(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
+                        void* stream, double* ms, int* launches) {
+  int rc = check_vec_args(h, 0, precision, nrhs);
+  if (rc) return rc;
+  if (!r || !z || !ms) {
+    set_error("null vector or output array");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  NNMG_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    set_error("nnmg_vcycle_profile cannot run inside a stream capture");
+    return NNMG_INVALID_ARG;
+  }
+  const int nl = (int)h->lv.size(), top = nl - 1;
+  const size_t n = (size_t)h->lv[top].rows * nrhs;
+  VcycleTimer P;
+  auto run = [&](auto tag, WorkSet<decltype(tag)>& W) -> int {
+    using T = decltype(tag);
+    int rr = ensure_work<T>(h);
+    if (rr) return rr;
+    for (int l = 1; l <= top; ++l) op_units<T>(h, l, nrhs, s);   // tune outside the timed launches
+    NNMG_CUDA(cudaMemcpyAsync(W.f[top], r, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (top == 0) NNMG_CUDA(cudaMemsetAsync(W.x[0], 0, n * sizeof(T), s));
+    NNMG_CUDA(enqueue_vcycle<T>(h, W.f[top], nrhs, s, &P));
+    NNMG_CUDA(cudaMemcpyAsync(z, W.x[top], n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    return NNMG_OK;
+  };
+  rc = precision == NNMG_F64 ? run(0.0, h->w64) : run(0.0f, h->w32);
+  if (rc) return rc;
+  NNMG_CUDA(cudaStreamSynchronize(s));
+  std::fill(ms, ms + (size_t)nl * NNMG_PROF_COLS, 0.0);
+  if (launches) std::fill(launches, launches + (size_t)nl * NNMG_PROF_COLS, 0);
+  for (const auto& m : P.marks) {
+    float t = 0.f;
+    NNMG_CUDA(cudaEventElapsedTime(&t, m.a, m.b));
+    int cols[2] = {m.col_component, m.col_kind};
+    const int nc = m.col_kind == m.col_component ? 1 : 2;
+    for (int c = 0; c < nc; ++c) {
+      ms[(size_t)m.level * NNMG_PROF_COLS + cols[c]] += t;
+      if (launches) ++launches[(size_t)m.level * NNMG_PROF_COLS + cols[c]];
+    }
   }
   return NNMG_OK;
 }

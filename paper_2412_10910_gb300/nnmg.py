@@ -253,6 +253,19 @@ def nnmg_vcycle(h, r, z, nrhs, stream=None, ncomp=1):
                             nrhs, _stream(stream)), "nnmg_vcycle")
 
 
+def nnmg_vcycle_profile(h, r, z, nrhs, stream=None, ncomp=1):
+    """One V-cycle as nnmg_vcycle, timed per level and component; returns
+    (ms, launches), numpy arrays [n_levels][len(_abi.PROF_COLUMNS)]."""
+    _need(h, nnmg_n_levels(h) - 1, r, nrhs, ncomp, "r")
+    nl = nnmg_n_levels(h)
+    ms = np.zeros((nl, len(_abi.PROF_COLUMNS)), dtype=np.float64)
+    cnt = np.zeros((nl, len(_abi.PROF_COLUMNS)), dtype=np.int32)
+    _check(_lib.nnmg_vcycle_profile(h, _prec(r), _dev(r, name="r"),
+                                    _dev(z, r.dtype, r.numel(), name="z"), nrhs, _stream(stream),
+                                    ms.ctypes.data, cnt.ctypes.data), "nnmg_vcycle_profile")
+    return ms, cnt
+
+
 def nnmg_pcg_solve(h, mode, b, x, nrhs, rtol=1e-8, maxit=200, stream=None, allow_fail=False,
                    ncomp=1):
     """Returns (status, iters[nrhs], relres[nrhs])."""
@@ -385,6 +398,11 @@ class Hierarchy:
 
     def vcycle(self, r, z):
         nnmg_vcycle(self.h, r, z, self._nrhs(r), ncomp=self.ncomp)
+
+    def vcycle_profile(self, r, z):
+        """(ms, launches) per level and component of one V-cycle (see
+        _abi.PROF_COLUMNS)."""
+        return nnmg_vcycle_profile(self.h, r, z, self._nrhs(r), ncomp=self.ncomp)
 
     def pcg(self, b, x, mode=_abi.FP32_MG_FP64_CG, rtol=1e-8, maxit=200, allow_fail=False):
         return nnmg_pcg_solve(self.h, mode, b, x, self._nrhs(b), rtol, maxit,
