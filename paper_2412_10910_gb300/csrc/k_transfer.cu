@@ -5,19 +5,23 @@
 // one mesh, Sec. 2 "Coarse grid solvers").
 //
 // Prolongation x_f += P x_c (Sec. 2, P[i,j] = phi^{l-1}_j(x_i); Sec. 3.2,
-// Eqs. local_evaluation, tensor_product_evaluation): one block per coarse cell
-// stages the cell's (k+1)^d coarse values for all channels in shared memory;
-// each (fine point, channel) pair tabulates the 1D Lagrange bases at its
-// reference point and contracts them direction by direction.  Every fine point
-// belongs to exactly one coarse cell, so its output is written once (no
-// atomics).
+// Eqs. local_evaluation, tensor_product_evaluation): the fine points are
+// grouped by coarse cell; at each point the 1D Lagrange bases are evaluated at
+// its reference coordinates and contracted with the cell's (k+1)^d coarse
+// values direction by direction.  Every fine point belongs to exactly one
+// coarse cell, so its output is written once (no atomics).
 //
 // Restriction r_c = P^T r_f (Sec. 2, Eq. residual2) in two deterministic
-// phases: (1) per coarse cell, each (local node, channel) pair sums
-// phi_j(xi_p) r_f(p) over the cell's fine points in their stored order into a
-// cell-local buffer; (2) per coarse node, the buffer entries of the cells that
-// share it are summed in ascending (cell, local) order.  No atomics: results
-// are bitwise reproducible.
+// phases: (1) per coarse cell, phi_j(xi_p) r_f(p) is summed over the cell's
+// fine points into a cell-local buffer, in an order fixed by the code;
+// (2) per coarse node, the buffer entries of the cells that share it are
+// summed in ascending (cell, local) order.  No atomics: results are bitwise
+// reproducible.
+//
+// Two forms of each: a register form (a warp per coarse cell, the cell's
+// values or buffer entries of one channel held by each thread; at most 64
+// nodes per cell) and a shared-memory form for 3D degree 4 (a block per
+// coarse cell stages the cell's values for all channels).
 #include <algorithm>
 #include <cstring>
 
@@ -38,7 +42,9 @@ __device__ __forceinline__ void lagrange1d(const Basis1D<T>& B, T xi, T* L) {
   }
 }
 
-// Fine points of a coarse cell are handled in chunks of kChunk: a cell holds
+// Shared-memory forms (3D degree 4, whose 125 coarse values or buffer entries
+// per channel do not fit a thread's registers).  Fine points of a coarse cell
+// are handled in chunks of kChunk: a cell holds
 // about (refinement ratio)^d points, ~66-68 for the 2.1-2.2x coarsening of the
 // configurations, so one chunk (one gather round, two barriers) covers it.
 constexpr int kChunk = 128;
@@ -154,6 +160,173 @@ __global__ void restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
   }
 }
 
+// Register forms (at most 64 coarse nodes per cell: 2D k <= 4, 3D k <= 3).
+// A coarse cell's fine points are split into P parts (points p0 + part,
+// p0 + part + P, ...), and each (cell, part, channel) goes to one thread.
+// With nch <= 32 channels a cell gets one warp: lane = part * nch + channel,
+// P = 32 / nch, and the 32 % nch remaining lanes idle; the parts of a cell are
+// combined by shuffles.  With more channels a cell gets nch threads (P = 1).
+// No shared memory and no barriers: a thread's loads are the cell's data and,
+// per point, its reference point, fine node and one value.
+constexpr int kRegNodes = 64;
+constexpr int kPts = 4;   // points per batch of loads
+__host__ __device__ inline int transfer_lanes(int nch) { return nch <= 32 ? 32 : nch; }
+
+// Prolongation: the thread keeps its channel's NL coarse values in registers
+// and evaluates the coarse polynomial at each of its points (the contraction
+// order of the shared-memory form).
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(128) prolong_reg_kernel(
+    const int32_t* __restrict__ coarse_cell_nodes, const T* __restrict__ xc, T* __restrict__ xf,
+    const int32_t* __restrict__ cell_pt_start, const int32_t* __restrict__ pt_node,
+    const T* __restrict__ pt_xi, int64_t n_cells, int nch, Basis1D<T> B) {
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lanes = transfer_lanes(nch), P = lanes / nch;
+  const int64_t c = e / lanes;
+  const int r = (int)(e - c * lanes), part = r / nch, ch = r - part * nch;
+  if (c >= n_cells || part >= P) return;
+  const int32_t* cn = coarse_cell_nodes + c * NL;
+  T u[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    const int node = cn[j];
+    u[j] = node >= 0 ? xc[(int64_t)node * nch + ch] : T(0);
+  }
+  const int p0 = cell_pt_start[c], p1 = cell_pt_start[c + 1];
+  // kPts points at a time: their indices, reference points and old fine
+  // values are loaded before any of them is evaluated
+  for (int p = p0 + part; p < p1; p += kPts * P) {
+    int node[kPts];
+    T xi[kPts][D], old[kPts];
+#pragma unroll
+    for (int b = 0; b < kPts; ++b) {
+      const int q = p + b * P;
+      node[b] = q < p1 ? pt_node[q] : -1;
+#pragma unroll
+      for (int d = 0; d < D; ++d) xi[b][d] = q < p1 ? pt_xi[(int64_t)q * D + d] : T(0);
+    }
+#pragma unroll
+    for (int b = 0; b < kPts; ++b) old[b] = node[b] >= 0 ? xf[(int64_t)node[b] * nch + ch] : T(0);
+#pragma unroll
+    for (int b = 0; b < kPts; ++b) {
+      if (node[b] < 0) continue;
+      T L[D][N];
+#pragma unroll
+      for (int d = 0; d < D; ++d) lagrange1d<N, T>(B, xi[b][d], L[d]);
+      T val = 0;
+      if constexpr (D == 2) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          T s = 0;
+#pragma unroll
+          for (int i = 0; i < N; ++i) s += L[0][i] * u[i + N * j];
+          val += L[1][j] * s;
+        }
+      } else {
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          T s1 = 0;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            T s0 = 0;
+#pragma unroll
+            for (int i = 0; i < N; ++i) s0 += L[0][i] * u[i + N * j + N * N * l];
+            s1 += L[1][j] * s0;
+          }
+          val += L[2][l] * s1;
+        }
+      }
+      xf[(int64_t)node[b] * nch + ch] = old[b] + val;
+    }
+  }
+}
+
+// Restriction phase one: the thread accumulates phi_m(xi_p) r_p over its
+// points for all NL local nodes m of the cell (sum-factorized outer product,
+// points in stored order); the P parts of a cell are then added by shuffles
+// in a fixed tree, so the result does not depend on scheduling.
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(128) restrict1_reg_kernel(
+    const T* __restrict__ rf, T* __restrict__ buf, const int32_t* __restrict__ cell_pt_start,
+    const int32_t* __restrict__ pt_node, const T* __restrict__ pt_xi, int64_t n_cells, int nch,
+    Basis1D<T> B) {
+  constexpr int N = K + 1;
+  constexpr int NL = D == 2 ? N * N : N * N * N;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lanes = transfer_lanes(nch), P = lanes / nch;
+  const int64_t c = e / lanes;
+  // with nch <= 32 a warp is exactly one cell: whole warps leave here together
+  if (c >= n_cells) return;
+  const int r = (int)(e - c * lanes), part = r / nch, ch = r - part * nch;
+  const bool idle = part >= P;                 // one of the 32 % nch spare lanes
+  T acc[NL];
+#pragma unroll
+  for (int m = 0; m < NL; ++m) acc[m] = 0;
+  const int p0 = cell_pt_start[c], p1 = cell_pt_start[c + 1];
+  for (int p = idle ? p1 : p0 + part; p < p1; p += kPts * P) {
+    int node[kPts];
+    T xi[kPts][D], rv[kPts];
+#pragma unroll
+    for (int b = 0; b < kPts; ++b) {
+      const int q = p + b * P;
+      node[b] = q < p1 ? pt_node[q] : -1;
+#pragma unroll
+      for (int d = 0; d < D; ++d) xi[b][d] = q < p1 ? pt_xi[(int64_t)q * D + d] : T(0);
+    }
+#pragma unroll
+    for (int b = 0; b < kPts; ++b) rv[b] = node[b] >= 0 ? rf[(int64_t)node[b] * nch + ch] : T(0);
+#pragma unroll
+    for (int b = 0; b < kPts; ++b) {
+      if (node[b] < 0) continue;
+      T L[D][N];
+#pragma unroll
+      for (int d = 0; d < D; ++d) lagrange1d<N, T>(B, xi[b][d], L[d]);
+      if constexpr (D == 2) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T w = L[1][j] * rv[b];
+#pragma unroll
+          for (int i = 0; i < N; ++i) acc[i + N * j] += L[0][i] * w;
+        }
+      } else {
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          const T w2 = L[2][l] * rv[b];
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const T w1 = L[1][j] * w2;
+#pragma unroll
+            for (int i = 0; i < N; ++i) acc[i + N * j + N * N * l] += L[0][i] * w1;
+          }
+        }
+      }
+    }
+  }
+  if (P > 1) {
+    // fixed tree over the parts: at step h, part q < h adds part q + h
+    int h = 1;
+    while (2 * h < P) h *= 2;
+    for (; h >= 1; h >>= 1) {
+      const bool take = part < h && part + h < P;
+#pragma unroll
+      for (int m = 0; m < NL; ++m) {
+        const T o = __shfl_down_sync(0xffffffffu, acc[m], h * nch);
+        if (take) acc[m] += o;
+      }
+    }
+  }
+  if (part == 0) {
+#pragma unroll
+    for (int m = 0; m < NL; ++m) buf[(c * NL + m) * nch + ch] = acc[m];
+  }
+}
+
+// Phase two: per (coarse node, channel) the buffer entries of the cells that
+// share the node, added in ascending list order (kBatch list entries and
+// their values loaded at a time, so the loads of one node overlap).
+constexpr int kBatch = 8;
 template <typename T>
 __global__ void restrict2_kernel(const T* __restrict__ buf, const int32_t* __restrict__ gstart,
                                  const int32_t* __restrict__ gpos, T* __restrict__ rc,
@@ -162,8 +335,19 @@ __global__ void restrict2_kernel(const T* __restrict__ buf, const int32_t* __res
   if (e >= n_nodes * nch) return;
   const int64_t node = e / nch;
   const int ch = (int)(e - node * nch);
+  const int k0 = gstart[node], k1 = gstart[node + 1];
   T s = 0;
-  for (int k = gstart[node]; k < gstart[node + 1]; ++k) s += buf[(int64_t)gpos[k] * nch + ch];
+  for (int k = k0; k < k1; k += kBatch) {
+    int pos[kBatch];
+    T v[kBatch];
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i) pos[i] = k + i < k1 ? gpos[k + i] : -1;
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i) v[i] = pos[i] >= 0 ? buf[(int64_t)pos[i] * nch + ch] : T(0);
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i)
+      if (k + i < k1) s += v[i];
+  }
   rc[e] = s;
 }
 
@@ -251,6 +435,7 @@ const double* xi_of<double>(const DevLevel& L) { return L.pt_xi64; }
 template <>
 const float* xi_of<float>(const DevLevel& L) { return L.pt_xi32; }
 
+
 // Opt a kernel in to `dyn` bytes of dynamic shared memory when its static
 // and dynamic shared memory together exceed the default 48 KB per block;
 // `granted` remembers the largest size already allowed for this kernel.
@@ -276,12 +461,18 @@ cudaError_t prolong_dk(const DevLevel& f, const DevLevel& c, const T* xc, T* xf,
   constexpr int N = K + 1;
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const size_t smem = (size_t)NL * nch * sizeof(T);
-  auto kern = prolong_kernel<D, K, T>;
-  static size_t granted = 0;
-  cudaError_t e = allow_smem(kern, smem, &granted);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)c.n_cells, 128, smem, s>>>(c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node,
-                                              xi_of<T>(f), nch, B);
+  if constexpr (NL <= kRegNodes) {
+    const int64_t threads = c.n_cells * transfer_lanes(nch);
+    prolong_reg_kernel<D, K, T><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
+        c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node, xi_of<T>(f), c.n_cells, nch, B);
+  } else {
+    auto kern = prolong_kernel<D, K, T>;
+    static size_t granted = 0;
+    cudaError_t e = allow_smem(kern, smem, &granted);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)c.n_cells, 128, smem, s>>>(c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node,
+                                                xi_of<T>(f), nch, B);
+  }
   return cudaGetLastError();
 }
 
@@ -293,12 +484,19 @@ cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* rc
   constexpr int N = K + 1;
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const size_t smem = (size_t)kChunk * nch * sizeof(T);
-  auto kern = restrict1_kernel<D, K, T>;
-  static size_t granted = 0;
-  cudaError_t e = allow_smem(kern, smem, &granted);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)c.n_cells, (unsigned)((NL / N * nch + 127) / 128));
-  kern<<<grid, 128, smem, s>>>(rf, scratch, f.cell_pt_start, f.pt_node, xi_of<T>(f), nch, B);
+  cudaError_t e;
+  if constexpr (NL <= kRegNodes) {
+    const int64_t threads = c.n_cells * transfer_lanes(nch);
+    restrict1_reg_kernel<D, K, T><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
+        rf, scratch, f.cell_pt_start, f.pt_node, xi_of<T>(f), c.n_cells, nch, B);
+  } else {
+    auto kern = restrict1_kernel<D, K, T>;
+    static size_t granted = 0;
+    e = allow_smem(kern, smem, &granted);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)c.n_cells, (unsigned)((NL / N * nch + 127) / 128));
+    kern<<<grid, 128, smem, s>>>(rf, scratch, f.cell_pt_start, f.pt_node, xi_of<T>(f), nch, B);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = c.n_nodes * nch;
