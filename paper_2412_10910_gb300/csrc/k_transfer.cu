@@ -19,9 +19,9 @@
 // reproducible.
 //
 // Two forms of each: a register form (a warp per coarse cell, the cell's
-// values or buffer entries of one channel held by each thread; at most 64
-// nodes per cell) and a shared-memory form for 3D degree 4 (a block per
-// coarse cell stages the cell's values for all channels).
+// values or buffer entries of one channel held by each thread; up to 128 FP32
+// or 64 FP64 values per cell) and a shared-memory form for FP64 3D degree 4
+// (a block per coarse cell stages the cell's values for all channels).
 #include <algorithm>
 #include <cstring>
 
@@ -42,8 +42,8 @@ __device__ __forceinline__ void lagrange1d(const Basis1D<T>& B, T xi, T* L) {
   }
 }
 
-// Shared-memory forms (3D degree 4, whose 125 coarse values or buffer entries
-// per channel do not fit a thread's registers).  Fine points of a coarse cell
+// Shared-memory forms (FP64 3D degree 4, whose 125 coarse values or buffer
+// entries per channel do not fit a thread's registers).  Fine points of a coarse cell
 // are handled in chunks of kChunk: a cell holds
 // about (refinement ratio)^d points, ~66-68 for the 2.1-2.2x coarsening of the
 // configurations, so one chunk (one gather round, two barriers) covers it.
@@ -160,7 +160,7 @@ __global__ void restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
   }
 }
 
-// Register forms (at most 64 coarse nodes per cell: 2D k <= 4, 3D k <= 3).
+// Register forms (FP32: every degree; FP64: 2D k <= 4, 3D k <= 3).
 // A coarse cell's fine points are split into P parts (points p0 + part,
 // p0 + part + P, ...), and each (cell, part, channel) goes to one thread.
 // With nch <= 32 channels a cell gets one warp: lane = part * nch + channel,
@@ -168,7 +168,13 @@ __global__ void restrict1_kernel(const T* __restrict__ rf, T* __restrict__ buf,
 // combined by shuffles.  With more channels a cell gets nch threads (P = 1).
 // No shared memory and no barriers: a thread's loads are the cell's data and,
 // per point, its reference point, fine node and one value.
-constexpr int kRegNodes = 64;
+// Register forms serve cells of at most kRegWords 4-byte words of values per
+// channel: 128 FP32 values (3D Q4) or 64 FP64 values.
+constexpr int kRegWords = 128;
+template <typename T>
+constexpr bool reg_transfer(int nl) {
+  return nl * (int)(sizeof(T) / 4) <= kRegWords;
+}
 constexpr int kPts = 4;   // points per batch of loads
 __host__ __device__ inline int transfer_lanes(int nch) { return nch <= 32 ? 32 : nch; }
 
@@ -461,7 +467,7 @@ cudaError_t prolong_dk(const DevLevel& f, const DevLevel& c, const T* xc, T* xf,
   constexpr int N = K + 1;
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const size_t smem = (size_t)NL * nch * sizeof(T);
-  if constexpr (NL <= kRegNodes) {
+  if constexpr (reg_transfer<T>(NL)) {
     const int64_t threads = c.n_cells * transfer_lanes(nch);
     prolong_reg_kernel<D, K, T><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
         c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node, xi_of<T>(f), c.n_cells, nch, B);
@@ -485,7 +491,7 @@ cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* rc
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const size_t smem = (size_t)kChunk * nch * sizeof(T);
   cudaError_t e;
-  if constexpr (NL <= kRegNodes) {
+  if constexpr (reg_transfer<T>(NL)) {
     const int64_t threads = c.n_cells * transfer_lanes(nch);
     restrict1_reg_kernel<D, K, T><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
         rf, scratch, f.cell_pt_start, f.pt_node, xi_of<T>(f), c.n_cells, nch, B);
