@@ -145,6 +145,8 @@ def operator_kernel_name(choice, k, dtype):
         return f"op_reg2_kernel<3,{k}> (paired FP32 register-resident)"
     if choice > 0:
         return f"op3d_kernel<{k},{dtype},1> ({choice} units per block)"
+    if choice <= -100:
+        return f"op3d_kernel<{k},f2,1> (paired FP32, {-100 - choice} (cell, pair) units per block)"
     return f"default rule for <3,{k},{dtype}>"
 
 

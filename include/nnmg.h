@@ -185,7 +185,8 @@ int nnmg_setup_seconds(const nnmg_handle* h, double* seconds);
  * (no counterpart in the paper: an implementation detail exposed for
  * profiling).  *choice: -1 register-resident kernel (one thread per cell and
  * column), -2 its paired FP32 form (one thread per cell and two columns), U > 0
- * shared-memory kernel with U (cell, column) units per block, 0 the default
+ * shared-memory kernel with U (cell, column) units per block, -100 - U its
+ * paired FP32 form (3D Poisson, U (cell, column pair) units), 0 the default
  * rule (not tuned yet, autotuning off, or first used inside a stream capture).
  * INVALID_ARG for a null handle or pointer, a bad level, precision or nrhs. */
 int nnmg_operator_choice(const nnmg_handle* h, int level, int precision, int nrhs, int* choice);

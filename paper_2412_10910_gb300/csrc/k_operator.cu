@@ -61,6 +61,23 @@ __device__ __forceinline__ T mac(T s, T m, T u) {
 }
 __device__ __forceinline__ f2 mac(f2 s, f2 m, f2 u) { return f2(__ffma2_rn(m.v, u.v, s.v)); }
 
+// The paired type reads and writes float pairs (two right-hand sides) and
+// FP32 metric terms; the other types read metric terms of their own type.
+template <>
+struct io_of<f2> {
+  using type = float2;
+};
+template <typename T>
+struct metric_type {
+  using type = T;
+};
+template <>
+struct metric_type<f2> {
+  using type = float;
+};
+__device__ __forceinline__ f2 to_arith(float2 v, f2) { return f2(v); }
+__device__ __forceinline__ void add_out(float2* p, f2 v) { atomicAdd(p, v.v); }
+
 // The two 1D matrices of the sweeps: S interpolates from the Lobatto nodes to
 // the Gauss points, Dg differentiates by collocation on the Gauss points.  For
 // odd N the middle Gauss point is the middle Lobatto node (both are 1/2), so
@@ -152,7 +169,8 @@ __device__ __forceinline__ void elastic_flux(const T (&g)[3][3], const T (&K)[3]
 }
 
 template <int K, typename T, int NC>
-__global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __restrict__ metric,
+__global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes,
+                            const typename metric_type<T>::type* __restrict__ metric,
                             const typename io_of<T>::type* __restrict__ x,
                             typename io_of<T>::type* __restrict__ y, int64_t n_cells, int nrhs,
                             int U, Basis1D<T> B, T lambda, T mu) {
@@ -174,7 +192,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
   // P0 + P1: gather the z-line (i=a, j=b) and interpolate along z in registers
 #pragma unroll
   for (int l = 0; l < N; ++l) dof[l] = act ? cell_nodes[cell * NQ + a + N * b + N2 * l] : -1;
-  const T* mc = metric + (act ? cell : 0) * NM * NQ;
+  const typename metric_type<T>::type* mc = metric + (act ? cell : 0) * NM * NQ;
   // Poisson: fetch the metric terms of this thread's quadrature column now, so
   // that their latency overlaps the first sweeps (used in P5)
   T Gp[NC == 1 ? 6 : 1][N];
@@ -182,7 +200,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
 #pragma unroll
     for (int q = 0; q < N; ++q)
 #pragma unroll
-      for (int m = 0; m < 6; ++m) Gp[m][q] = act ? mc[m * NQ + a + N * b + N2 * q] : T(0);
+      for (int m = 0; m < 6; ++m) Gp[m][q] = act ? T(mc[m * NQ + a + N * b + N2 * q]) : T(0);
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -251,9 +269,15 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
         T G[6];
 #pragma unroll
         for (int m = 0; m < 6; ++m) G[m] = Gp[m][q];
-        S(1, idx) = G[0] * gx + G[1] * gy + G[2] * g3;
-        S(2, idx) = G[1] * gx + G[3] * gy + G[4] * g3;
-        gz[0][q] = G[2] * gx + G[4] * gy + G[5] * g3;
+        if constexpr (std::is_same<T, f2>::value) {
+          S(1, idx) = mac(mac(G[0] * gx, G[1], gy), G[2], g3);
+          S(2, idx) = mac(mac(G[1] * gx, G[3], gy), G[4], g3);
+          gz[0][q] = mac(mac(G[2] * gx, G[4], gy), G[5], g3);
+        } else {
+          S(1, idx) = G[0] * gx + G[1] * gy + G[2] * g3;
+          S(2, idx) = G[1] * gx + G[3] * gy + G[4] * g3;
+          gz[0][q] = G[2] * gx + G[4] * gy + G[5] * g3;
+        }
       } else {
         T g[3][3], Km[3][3], F[3][3];
 #pragma unroll
@@ -263,7 +287,7 @@ __global__ void op3d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
           g[c][2] = gz[c][q];
         }
 #pragma unroll
-        for (int m = 0; m < 9; ++m) Km[m / 3][m % 3] = act ? mc[m * NQ + idx] : T(0);
+        for (int m = 0; m < 9; ++m) Km[m / 3][m % 3] = act ? T(mc[m * NQ + idx]) : T(0);
         elastic_flux(g, Km, lambda, mu, F);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -690,7 +714,8 @@ inline int unit_candidates(int lines, int nrhs, int max_threads, size_t per_unit
 }
 
 template <int K, typename T, int NC>
-cudaError_t run3d(const DevLevel& L, const T* metric, const typename io_of<T>::type* x,
+cudaError_t run3d(const DevLevel& L, const typename metric_type<T>::type* metric,
+                  const typename io_of<T>::type* x,
                   typename io_of<T>::type* y, int nrhs, double lambda, double mu, cudaStream_t s,
                   int units) {
   constexpr int N = K + 1;
@@ -766,6 +791,12 @@ cudaError_t run_reg2(const DevLevel& L, const float* metric, const float* x, flo
 // choices), units = 0 for the default: the register kernel where it applies
 // in FP32 and FP64, the shared-memory kernel in double-word arithmetic (whose
 // register kernel, at 255 registers, measured 1.9x slower on 3D Q2).
+// units <= kPairedSmem selects the paired FP32 form of the 3D Poisson
+// shared-memory kernel (two right-hand sides per thread, packed FP32
+// instructions) with kPairedSmem - units (cell, pair) units per block; it
+// runs for an even nrhs on 8-byte aligned vectors (otherwise the default).
+constexpr int kPairedSmem = -100;
+
 template <typename T>
 bool reg_eligible(const DevLevel& L) {
   return L.ncomp == 1 && (L.dim == 2 || L.k <= 2);
@@ -784,6 +815,20 @@ cudaError_t launch_operator_impl(const DevLevel& L, const typename io_of<T>::typ
 #define NNMG_REG2(D, K) if (L.dim == D && L.k == K) return run_reg2<D, K>(L, m, x, y, nrhs, s);
       NNMG_REG2(2, 1) NNMG_REG2(2, 2) NNMG_REG2(2, 3) NNMG_REG2(2, 4) NNMG_REG2(3, 1) NNMG_REG2(3, 2)
 #undef NNMG_REG2
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (units <= kPairedSmem && L.dim == 3 && L.ncomp == 1 && nrhs % 2 == 0 &&
+        (uintptr_t)x % 8 == 0 && (uintptr_t)y % 8 == 0) {
+      const float2* x2 = reinterpret_cast<const float2*>(x);
+      float2* y2 = reinterpret_cast<float2*>(y);
+      const int U = kPairedSmem - units;
+      switch (L.k) {
+        case 1: return run3d<1, f2, 1>(L, m, x2, y2, nrhs / 2, 0.0, 0.0, s, U);
+        case 2: return run3d<2, f2, 1>(L, m, x2, y2, nrhs / 2, 0.0, 0.0, s, U);
+        case 3: return run3d<3, f2, 1>(L, m, x2, y2, nrhs / 2, 0.0, 0.0, s, U);
+        case 4: return run3d<4, f2, 1>(L, m, x2, y2, nrhs / 2, 0.0, 0.0, s, U);
+      }
     }
   }
   constexpr bool reg_default = !std::is_same<T, dw>::value;
@@ -846,7 +891,21 @@ int operator_unit_candidates(const DevLevel& L, int nrhs, int* out, int max_out)
   int n = 0;
   if (reg_eligible<T>(L) && max_out > 0) out[n++] = -1;   // the register-resident kernel
   if (sizeof(T) == 4 && reg_eligible<T>(L) && nrhs % 2 == 0 && n < max_out) out[n++] = -2;
-  return n + unit_candidates(lines, nrhs, mt, per_unit, out + n, max_out - n);
+  n += unit_candidates(lines, nrhs, mt, per_unit, out + n, max_out - n);
+  if (sizeof(T) == 4 && L.dim == 3 && L.ncomp == 1 && nrhs % 2 == 0 && n < max_out) {
+    int mt2 = 256;
+#define NNMG_C2(K) if (L.k == K) mt2 = kernel_max_threads(op3d_kernel<K, f2, 1>);
+    NNMG_C2(1) NNMG_C2(2) NNMG_C2(3) NNMG_C2(4)
+#undef NNMG_C2
+    // (cell, pair) units per block: from half the unpaired kernel's smallest
+    // block (the same cells per block) upwards, doubling
+    const int npair = nrhs / 2;
+    const int u0 = 32 - (32 % nrhs);
+    for (int U = std::max(npair, std::max(nrhs, u0 / 4 / nrhs * nrhs) / 2);
+         U * lines <= mt2 && (size_t)U * per_unit * 2 <= kMaxSmem && n < max_out; U *= 2)
+      if (U * lines >= 32) out[n++] = kPairedSmem - U;
+  }
+  return n;
 }
 
 template cudaError_t launch_operator<float>(const DevLevel&, const float*, float*, int, double,

@@ -166,13 +166,13 @@ int ensure_pcg(nnmg_handle* h) {
 // ------------------------------------------------------------------ autotuner
 // Operator kernel choice for (level, precision, nrhs): -1 the register-resident
 // kernel, -2 its paired FP32 form, U > 0 the shared-memory kernel with U units
-// per block, 0 the default rule.  On first use every legal choice is timed
-// (one warm-up and three timed launches on scratch vectors, CUDA events) and
-// the fastest is kept for the handle's lifetime.  Never runs during stream
-// capture (the default rule is used then); NNMG_AUTOTUNE=0 in the
-// environment keeps the default rule, NNMG_OP_CHOICE=<c> forces choice c on
-// every level (a choice that does not apply to a level falls back to the
-// default there).
+// per block, -100 - U its paired FP32 form, 0 the default rule.  On first use
+// every legal choice is timed (two warm-ups and six timed launches on scratch
+// vectors, CUDA events) and the fastest is kept for the handle's lifetime.
+// Never runs during stream capture (the default rule is used then);
+// NNMG_AUTOTUNE=0 in the environment keeps the default rule, NNMG_OP_CHOICE=<c>
+// forces choice c on every level (a choice that does not apply to a level
+// falls back to the default there).
 template <typename T, typename Launch>
 int tune_units(nnmg_handle* h, int level, int prec_key, int nrhs, cudaStream_t s, Launch launch) {
   auto key = std::make_tuple(level, prec_key, nrhs);
@@ -191,8 +191,8 @@ int tune_units(nnmg_handle* h, int level, int prec_key, int nrhs, cudaStream_t s
   if (!enabled || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
     return 0;
   const DevLevel& L = h->lv[level];
-  int cand[8];
-  const int nc = operator_unit_candidates<T>(L, nrhs, cand, 8);
+  int cand[16];
+  const int nc = operator_unit_candidates<T>(L, nrhs, cand, 16);
   int best = 0;
   if (nc > 1 && L.n_cells > 0) {
     using IO = std::conditional_t<sizeof(T) == 4, float, double>;
@@ -205,8 +205,9 @@ int tune_units(nnmg_handle* h, int level, int prec_key, int nrhs, cudaStream_t s
       float best_ms = 1e30f;
       for (int c = 0; c < nc; ++c) {
         bool ok = launch(L, x, y, cand[c]) == cudaSuccess;
+        ok = ok && launch(L, x, y, cand[c]) == cudaSuccess;
         ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
-        for (int r = 0; r < 3 && ok; ++r) ok = launch(L, x, y, cand[c]) == cudaSuccess;
+        for (int r = 0; r < 6 && ok; ++r) ok = launch(L, x, y, cand[c]) == cudaSuccess;
         ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
         float ms = 0.f;
         if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {

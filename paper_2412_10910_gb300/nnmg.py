@@ -377,7 +377,8 @@ class Hierarchy:
 
     def operator_choice(self, level, precision, nrhs):
         """-1 register kernel, -2 paired FP32 register kernel, U > 0 shared-memory
-        kernel with U units per block, 0 default rule / not chosen yet."""
+        kernel with U units per block, -100 - U its paired FP32 form, 0 default
+        rule / not chosen yet."""
         return nnmg_operator_choice(self.h, level, precision, nrhs)
 
     def load_vector(self, level, f, b, col=0, per_qp=False):

@@ -1,9 +1,11 @@
 """Every operator kernel variant against the FP64 oracle.
 
 The autotuner picks among the register-resident kernel (-1), its paired FP32
-form (-2, two right-hand sides per thread in packed FP32 instructions) and the
+form (-2, two right-hand sides per thread in packed FP32 instructions), the
 shared-memory kernel (units > 0; an unusable unit count keeps the default
-block); NNMG_OP_CHOICE pins one choice for a whole hierarchy, so each variant
+block) and its paired FP32 form for 3D Poisson (-100 - U: U (cell, pair)
+units per block; an odd nrhs, 2D levels and the other arithmetic types take
+the default); NNMG_OP_CHOICE pins one choice for a whole hierarchy, so each variant
 is checked on every level here whatever the timings would pick.  Tolerances
 as in test_gpu_parity.py.
 """
@@ -17,7 +19,7 @@ torch = pytest.importorskip("torch")
 
 # cases with register-eligible levels: 2D Q1-Q4, 3D Q1-Q2, odd and even nrhs
 NAMES = ["c1_q1", "c1_q3", "c1_q2_16rhs", "c1_q4_5rhs", "c2_q1_3lev", "c2_q2_3lev", "c3_q4_pmg"]
-CHOICES = {"register": -1, "paired": -2, "shared": 1000000}
+CHOICES = {"register": -1, "paired": -2, "shared": 1000000, "shared_paired": -108}
 TOL = {"f64": 1e-12, "f32": 2e-5, "dw": 1e-12}
 
 
@@ -57,14 +59,15 @@ def test_operator_variant(oracle, choice, dtype, monkeypatch):
         H.close()
 
 
-def test_paired_kernel_falls_back_on_unaligned_vectors(monkeypatch):
-    """The paired kernel reads float pairs; vectors that start 4 bytes off an
-    8-byte boundary must go to the unpaired kernel and give the same result."""
+@pytest.mark.parametrize("choice", ["paired", "shared_paired"])
+def test_paired_kernel_falls_back_on_unaligned_vectors(choice, monkeypatch):
+    """The paired kernels read float pairs; vectors that start 4 bytes off an
+    8-byte boundary must go to an unpaired kernel and give the same result."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     name = "c2_q2_3lev"
     levels, O = oracle_case(name)
-    monkeypatch.setenv("NNMG_OP_CHOICE", "-2")
+    monkeypatch.setenv("NNMG_OP_CHOICE", str(CHOICES[choice]))
     H = gpu_case(name, levels)
     try:
         nrhs = CASES[name][5]
@@ -89,7 +92,7 @@ def test_paired_kernel_falls_back_on_unaligned_vectors(monkeypatch):
         H.close()
 
 
-@pytest.mark.parametrize("choice", ["register", "paired"])
+@pytest.mark.parametrize("choice", ["register", "paired", "shared_paired"])
 def test_vcycle_and_pcg_with_variant(choice, monkeypatch):
     """The captured V-cycle and PCG graphs with a pinned kernel variant."""
     if not torch.cuda.is_available():
