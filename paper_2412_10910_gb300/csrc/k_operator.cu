@@ -13,8 +13,10 @@
 // contiguous right-hand sides and neighbouring cells.  A thread keeps one
 // line of k+1 values in registers per sweep; sweeps along other directions go
 // through shared memory laid out [array][point][unit] (bank-conflict free).
-// Dirichlet nodes carry index -1: read as 0, never written.  y must be zero on
-// entry (scatter is atomic).
+// In the paired FP32 form (T = f2) a unit is a (cell, pair of right-hand
+// sides) and every value a float pair.  The register-resident kernels further
+// down keep a whole cell of one unit in a thread.  Dirichlet nodes carry index
+// -1: read as 0, never written.  y must be zero on entry (scatter is atomic).
 #include <algorithm>
 #include <type_traits>
 
