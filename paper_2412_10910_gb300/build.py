@@ -27,8 +27,8 @@ def _newer(src, obj):
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "nnmg_internal.h"),
-            os.path.join(HERE, "..", "include", "nnmg.h")]
+    deps = [src, os.path.join(HERE, "..", "include", "nnmg.h")]
+    deps += [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
