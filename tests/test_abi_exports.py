@@ -43,3 +43,19 @@ def test_invalid_arguments_rejected_without_gpu_work():
     d = (_abi.LevelDesc * 1)()
     assert lib.nnmg_setup_hierarchy(d, 1, C.byref(o), None, C.byref(h)) == _abi.INVALID_ARG
     assert lib.nnmg_n_levels(None) == 0 and lib.nnmg_hierarchy_bytes(None) == 0
+
+
+def test_profile_columns_match_header():
+    """The Python names of nnmg_vcycle_profile's columns follow the header's
+    NNMG_PROF_* indices (the paper's six V-cycle components, then the two
+    kernel classes)."""
+    text = open(HEADER).read()
+    idx = {m.group(1): int(m.group(2))
+           for m in re.finditer(r"#define NNMG_PROF_([A-Z]+)\s+(\d+)", text)}
+    assert idx.pop("COLS") == len(_abi.PROF_COLUMNS)
+    names = {"PRE": "pre_smoother", "RESIDUAL": "residual", "RESTRICT": "restrictor",
+             "COARSE": "coarse_solver", "PROLONG": "prolongator", "POST": "post_smoother",
+             "OPERATOR": "operator", "VECTOR": "vector"}
+    assert sorted(idx) == sorted(names)
+    for k, i in idx.items():
+        assert _abi.PROF_COLUMNS[i] == names[k], k
