@@ -302,7 +302,8 @@ def run_reference(args, rank, world):
 
 def run_configs(args, rank):
     """Every configuration: setup time, then p50/p99 of timed solves (after
-    warm-up) in both modes, one JSON line per configuration."""
+    warm-up) in the three modes, the per-level V-cycle breakdown and the fine
+    level's kernels against HBM, one JSON line per configuration."""
     import numpy as np
     import torch
     from paper_2412_10910_gb300 import _abi, nnmg
@@ -370,6 +371,12 @@ def run_configs(args, rank):
                         "solves": steps, "iterations": [int(i) for i in its],
                         "max_relres": float(max(rel)),
                         "solved_dofs_per_s": nfree * cfg["ncomp"] * nrhs / (med / 1e3)}
+        # FP32 V-cycle per level and component, and the fine level's kernels
+        # against the measured HBM bandwidth
+        peaks, _ = _peaks()
+        out["vcycle_breakdown_ms"], out["fine_level_kernels_hbm"] = vcycle_kernel_table(
+            H, degs or [cfg["degree"]] * H.n_levels, cfg["ncomp"], nrhs, cfg["cheb"],
+            peaks["hbm_gbs"])
         if rank == 0:
             print(json.dumps(out), flush=True)
         H.close()
