@@ -24,6 +24,7 @@
 // (a block per coarse cell stages the cell's values for all channels).
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "nnmg_internal.h"
 
@@ -182,10 +183,10 @@ __host__ __device__ inline int transfer_lanes(int nch) { return nch <= 32 ? 32 :
 // and evaluates the coarse polynomial at each of its points (the contraction
 // order of the shared-memory form).
 template <int D, int K, typename T>
-__global__ void __launch_bounds__(128) prolong_reg_kernel(
+__device__ __forceinline__ void prolong_reg_body(
     const int32_t* __restrict__ coarse_cell_nodes, const T* __restrict__ xc, T* __restrict__ xf,
     const int32_t* __restrict__ cell_pt_start, const int32_t* __restrict__ pt_node,
-    const T* __restrict__ pt_xi, int64_t n_cells, int nch, Basis1D<T> B) {
+    const T* __restrict__ pt_xi, int64_t n_cells, int nch, const Basis1D<T>& B) {
   constexpr int N = K + 1;
   constexpr int NL = D == 2 ? N * N : N * N * N;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,6 +248,28 @@ __global__ void __launch_bounds__(128) prolong_reg_kernel(
       xf[(int64_t)node[b] * nch + ch] = old[b] + val;
     }
   }
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(128) prolong_reg_kernel(
+    const int32_t* __restrict__ coarse_cell_nodes, const T* __restrict__ xc, T* __restrict__ xf,
+    const int32_t* __restrict__ cell_pt_start, const int32_t* __restrict__ pt_node,
+    const T* __restrict__ pt_xi, int64_t n_cells, int nch, Basis1D<T> B) {
+  prolong_reg_body<D, K, T>(coarse_cell_nodes, xc, xf, cell_pt_start, pt_node, pt_xi, n_cells,
+                            nch, B);
+}
+
+// The 3D Q4 FP32 instance bounded to three blocks per SM: 168 registers
+// instead of 217 (125 coarse values per thread), 12 warps per SM instead of
+// 8; 0.197 vs 0.233 ms on config 3's finest pair.  (The same bound on the
+// smaller instances slows them: config 2's Q2, 0.058 vs 0.053 ms.)
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(128, 3) prolong_reg_kernel_3b(
+    const int32_t* __restrict__ coarse_cell_nodes, const T* __restrict__ xc, T* __restrict__ xf,
+    const int32_t* __restrict__ cell_pt_start, const int32_t* __restrict__ pt_node,
+    const T* __restrict__ pt_xi, int64_t n_cells, int nch, Basis1D<T> B) {
+  prolong_reg_body<D, K, T>(coarse_cell_nodes, xc, xf, cell_pt_start, pt_node, pt_xi, n_cells,
+                            nch, B);
 }
 
 // Restriction phase one: the thread accumulates phi_m(xi_p) r_p over its
@@ -469,8 +492,13 @@ cudaError_t prolong_dk(const DevLevel& f, const DevLevel& c, const T* xc, T* xf,
   const size_t smem = (size_t)NL * nch * sizeof(T);
   if constexpr (reg_transfer<T>(NL)) {
     const int64_t threads = c.n_cells * transfer_lanes(nch);
-    prolong_reg_kernel<D, K, T><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
-        c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node, xi_of<T>(f), c.n_cells, nch, B);
+    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    if constexpr (D == 3 && K == 4 && std::is_same<T, float>::value)
+      prolong_reg_kernel_3b<D, K, T><<<blocks, 128, 0, s>>>(
+          c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node, xi_of<T>(f), c.n_cells, nch, B);
+    else
+      prolong_reg_kernel<D, K, T><<<blocks, 128, 0, s>>>(
+          c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node, xi_of<T>(f), c.n_cells, nch, B);
   } else {
     auto kern = prolong_kernel<D, K, T>;
     static size_t granted = 0;
