@@ -167,12 +167,16 @@ class Server:
     """Admits requests by device-memory budget and runs all families' engines."""
 
     def __init__(self, families: dict, budget_bytes: int, nslots=16, mode=_abi.FP32_MG_FP64_CG,
-                 rtol=1e-8, maxit=200):
+                 rtol=1e-8, maxit=200, engine_factory=None):
         self.families = families
         self.budget = budget_bytes
         self.kw = dict(nslots=nslots, mode=mode, rtol=rtol, maxit=maxit)
         self.engines: dict[str, FamilyEngine] = {}
         self.evictions = 0
+        # builds a family's engine: FamilyEngine unless a caller substitutes
+        # its own (same constructor arguments, bytes(), busy(), close(),
+        # last_used)
+        self._make = engine_factory or FamilyEngine
 
     def used_bytes(self):
         return sum(e.bytes() for e in self.engines.values())
@@ -185,7 +189,7 @@ class Server:
         while True:
             idle = [e for e in self.engines.values() if not e.busy()]
             if eng is None:
-                eng = FamilyEngine(name, self.families[name], **self.kw)
+                eng = self._make(name, self.families[name], **self.kw)
             if self.used_bytes() + eng.bytes() <= self.budget:
                 self.engines[name] = eng
                 return eng

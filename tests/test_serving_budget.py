@@ -1,0 +1,73 @@
+"""Host logic of the serving loop: families are built under a device-memory
+budget, idle families are evicted least recently used first, a family that
+does not fit waits while every built family is busy, and a family larger
+than the whole budget is an error.  The engines are stand-ins with the
+interface the server uses (bytes, busy, close, last_used), so no GPU work is
+involved."""
+import pytest
+
+from paper_2412_10910_gb300.serving import Server
+
+
+class FakeEngine:
+    sizes = {}
+    clock = [0.0]
+
+    def __init__(self, name, spec, **kw):
+        self.name = name
+        self.kw = kw
+        self.is_busy = False
+        self.closed = False
+        FakeEngine.clock[0] += 1.0
+        self.last_used = FakeEngine.clock[0]
+
+    def bytes(self):
+        return FakeEngine.sizes[self.name]
+
+    def busy(self):
+        return self.is_busy
+
+    def close(self):
+        self.closed = True
+
+
+def _server(sizes, budget):
+    FakeEngine.sizes = dict(sizes)
+    return Server({n: None for n in sizes}, budget_bytes=budget, engine_factory=FakeEngine)
+
+
+def test_families_fill_the_budget_then_evict_least_recently_used():
+    s = _server({"a": 40, "b": 40, "c": 40}, 100)
+    a, b = s.engine("a"), s.engine("b")
+    assert s.used_bytes() == 80 and s.evictions == 0
+    assert s.engine("a") is a                      # cached, not rebuilt
+    a.last_used, b.last_used = 10.0, 5.0           # b is the least recently used
+    c = s.engine("c")
+    assert c is not None and b.closed and not a.closed
+    assert sorted(s.engines) == ["a", "c"] and s.evictions == 1
+    assert s.used_bytes() <= 100
+
+
+def test_busy_families_are_not_evicted_and_the_newcomer_waits():
+    s = _server({"a": 60, "b": 60}, 100)
+    a = s.engine("a")
+    a.is_busy = True
+    assert s.engine("b") is None                   # must wait, nothing evicted
+    assert not a.closed and s.evictions == 0 and list(s.engines) == ["a"]
+    a.is_busy = False
+    b = s.engine("b")
+    assert b is not None and a.closed and s.evictions == 1
+
+
+def test_a_family_larger_than_the_budget_is_an_error():
+    s = _server({"big": 500}, 100)
+    with pytest.raises(MemoryError):
+        s.engine("big")
+
+
+def test_server_passes_the_solver_settings_to_its_engines():
+    s = _server({"a": 1}, 100)
+    e = s.engine("a")
+    assert e.kw == {"nslots": 16, "mode": 1, "rtol": 1e-8, "maxit": 200}
+    s.close()
+    assert e.closed and not s.engines
