@@ -147,6 +147,17 @@ size_t nnmg_hierarchy_bytes(const nnmg_handle* h);
 /* Device bytes the work buffers of one solve with nrhs columns will add. */
 size_t nnmg_solve_bytes(const nnmg_handle* h, int nrhs);
 
+/* The same two sizes before anything is built (no counterpart in the paper:
+ * it serves admission by a device-memory budget).  From the level
+ * descriptions and options of nnmg_setup_hierarchy, on the host only (it
+ * numbers the nodes of every level; no CUDA call, no device allocation):
+ * *hierarchy_bytes (may be NULL) = what nnmg_hierarchy_bytes will report after
+ * setup; *solve_bytes (may be NULL) = nnmg_solve_bytes(h, nrhs) of that
+ * hierarchy.  Errors: INVALID_ARG (bad levels, options or nrhs outside
+ * 1..16), BAD_MESH (non-conforming mesh), OUT_OF_MEMORY (host). */
+int nnmg_estimate_bytes(const nnmg_level_desc* levels, int n_levels, const nnmg_options* opt,
+                        int nrhs, size_t* hierarchy_bytes, size_t* solve_bytes);
+
 /* Host copies of setup products of a level:
  * support points x_i = F_K(xi_i) [n_nodes][dim] (Sec. 2 Eq. pointwise);
  * constrained flags [n_nodes]; cell-to-node map [n_cells][(k+1)^d];
@@ -222,14 +233,18 @@ int nnmg_restrict(nnmg_handle* h, int fine_level, int precision, const void* fin
 /* coarse = P^T fine, as nnmg_restrict, without allocating anything.  The paper
  * has no counterpart: this entry point exists for callers that must not
  * allocate device memory while they run (allocator-free real-time loops,
- * memory handed out by an external pool or budget, host callbacks).  Its
- * scratch is a fixed 64 MiB array inside the library, held by every GPU that
- * loads the library until the process exits; the call fails with INVALID_ARG
- * when coarse cells x (k+1)^d x components x nrhs x value size exceeds it.
- * The array is shared by all calls: calls that overlap on the GPU race, so
- * order them on one stream.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  Nothing
- * needs clearing between calls. */
+ * memory handed out by an external pool or budget, host callbacks, where
+ * cudaMalloc may not be called).  Its scratch is a fixed 64 MiB array inside
+ * the library, held by every GPU that loads the library until the process
+ * exits; the call fails with INVALID_ARG when coarse cells x (k+1)^d x
+ * components x nrhs x value size exceeds it.  The array's device address is
+ * looked up by nnmg_setup_hierarchy (with the hierarchy's device current) and
+ * kept with the handle, so even the first call allocates nothing; call it
+ * with that device current (INVALID_ARG otherwise).  A device reset ends the
+ * handle: set up a new one.  The array is shared by all calls: calls that
+ * overlap on the GPU race, so order them on one stream.  Nothing needs
+ * clearing between calls: the first phase writes every entry the second
+ * reads. */
 int nnmg_restrict_noalloc(nnmg_handle* h, int fine_level, int precision, const void* fine,
                           void* coarse, int nrhs, void* stream);
 

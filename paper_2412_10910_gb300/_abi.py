@@ -37,6 +37,8 @@ PROTOTYPES = {
                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "nnmg_hierarchy_bytes": (C.c_size_t, [C.c_void_p]),
     "nnmg_solve_bytes": (C.c_size_t, [C.c_void_p, C.c_int]),
+    "nnmg_estimate_bytes": (C.c_int, [C.POINTER(LevelDesc), C.c_int, C.POINTER(Options), C.c_int,
+                                      C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "nnmg_support_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_constrained_nodes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_cell_nodes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),

@@ -11,60 +11,49 @@
 // calls cudaMalloc, cudaFree or any allocating routine.
 //
 // Costs and limits: every GPU that loads the library holds the array
-// (kNoAllocScratchBytes) until the process exits.  The array is shared by all
+// (kNoAllocScratchBytes) until the process exits.  The array's device address
+// is looked up when a hierarchy is set up (with its device current) and kept
+// with the handle, so the call must be made with that device current; a
+// device reset frees the hierarchy's memory and the array together, and the
+// handle must not be used after it (set up a new one).  The array is shared by all
 // calls: two calls that overlap on the GPU (different streams, or different
 // host threads without ordering) race on it and give wrong results; serialize
 // them on one stream.  The array keeps whatever the last call left; nothing
 // needs clearing, because the first phase writes every entry that the second
 // phase reads.
-#include <mutex>
-
 #include "nnmg_internal.h"
 
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_restrict_scratch[kNoAllocScratchBytes];
 
-// Device address of g_restrict_scratch per device.  Host code cannot use the
-// symbol itself (on the host it names a stand-in, not device memory), so the
-// address is looked up once per device with that device current.
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mutex;
+}  // namespace
 
-int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    nnmg::set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+namespace nnmg {
+// Device address of g_restrict_scratch on the current device.  Host code cannot
+// use the symbol itself (on the host it names a stand-in, not device memory).
+// nnmg_setup_hierarchy calls this once per hierarchy, with the hierarchy's
+// device current, and keeps the address with the handle; the lookup also makes
+// the runtime load the array onto that device then, so a later
+// nnmg_restrict_noalloc allocates nothing, not even on its first call.
+int noalloc_scratch_lookup(void** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_restrict_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     return NNMG_CUDA_ERROR;
   }
-  if (dev < 0 || dev >= kMaxDevices) {
-    nnmg::set_error("device ordinal too large for the scratch address table");
-    return NNMG_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_restrict_scratch);
-    if (e != cudaSuccess || !p) {
-      nnmg::set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-      return NNMG_CUDA_ERROR;
-    }
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return NNMG_OK;
 }
 
-}  // namespace
-
-// Defined with the other entry points: the handle's level data.
-namespace nnmg {
+// Defined with the other entry points: the handle's level data, its device
+// and the scratch address looked up at its setup.
 const DevLevel* handle_level(const nnmg_handle* h, int level);
 int handle_max_nrhs(const nnmg_handle* h);
+int handle_device(const nnmg_handle* h, void** noalloc_scratch);
 }  // namespace nnmg
 
 extern "C" int nnmg_restrict_noalloc(nnmg_handle* h, int fine_level, int precision,
@@ -91,8 +80,14 @@ extern "C" int nnmg_restrict_noalloc(nnmg_handle* h, int fine_level, int precisi
     return NNMG_INVALID_ARG;
   }
   void* scratch = nullptr;
-  int rc = scratch_address(&scratch);
-  if (rc != NNMG_OK) return rc;
+  const int hdev = handle_device(h, &scratch);
+  int dev = -1;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess || dev != hdev || !scratch) {
+    set_error("nnmg_restrict_noalloc: call with the hierarchy's device current (device " +
+              std::to_string(hdev) + ", current " + std::to_string(dev) + ")");
+    return NNMG_INVALID_ARG;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if (precision == NNMG_F64)

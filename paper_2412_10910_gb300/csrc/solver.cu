@@ -30,6 +30,8 @@ struct WorkSet {
 
 struct nnmg_handle {
   nnmg_options opt;
+  int device = -1;                  // the device current at setup
+  void* noalloc_scratch = nullptr;  // device address of nnmg_restrict_noalloc's array there
   std::vector<DevLevel> lv;
   cudaStream_t cap = nullptr;
   std::vector<void*> allocs;
@@ -836,7 +838,86 @@ const DevLevel* handle_level(const nnmg_handle* h, int level) {
   return &h->lv[level];
 }
 int handle_max_nrhs(const nnmg_handle* h) { return h ? h->opt.max_nrhs : 0; }
+int handle_device(const nnmg_handle* h, void** noalloc_scratch) {
+  *noalloc_scratch = h ? h->noalloc_scratch : nullptr;
+  return h ? h->device : -1;
+}
+int noalloc_scratch_lookup(void** out);
 }  // namespace nnmg
+
+namespace {
+// Sizes that decide the device memory of a hierarchy, from a level's mesh and
+// host numbering alone: used by nnmg_estimate_bytes before anything is
+// allocated, and by nnmg_solve_bytes.
+struct LevelPlan {
+  int dim = 0, k = 0, ncomp = 1, nloc = 0, nmetric = 0;
+  int64_t n_vertices = 0, n_cells = 0, n_nodes = 0, rows = 0, n_free_nodes = 0;
+  int64_t gather_entries = 0;   // cell-local slots holding a free node
+};
+
+LevelPlan level_plan(int dim, int k, int ncomp, int64_t nv, int64_t nc, const HostNumbering& num) {
+  LevelPlan p;
+  p.dim = dim;
+  p.k = k;
+  p.ncomp = ncomp;
+  p.nloc = dim == 2 ? (k + 1) * (k + 1) : (k + 1) * (k + 1) * (k + 1);
+  p.nmetric = ncomp == 1 ? dim * (dim + 1) / 2 : dim * dim;
+  p.n_vertices = nv;
+  p.n_cells = nc;
+  p.n_nodes = num.n_nodes;
+  p.rows = num.n_nodes * ncomp;
+  for (auto c : num.constrained) p.n_free_nodes += c ? 0 : 1;
+  for (auto n : num.cell_nodes) p.gather_entries += num.constrained[n] ? 0 : 1;
+  return p;
+}
+
+// One dalloc of `count` elements of T (at least one, as dalloc does).
+template <typename T>
+size_t bytes_of(int64_t count) {
+  return (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+}
+
+// The device bytes nnmg_setup_hierarchy allocates (what nnmg_hierarchy_bytes
+// reports right after setup), allocation by allocation: setup_level,
+// setup_transfer, setup_gather and setup_coarse.
+size_t planned_hierarchy_bytes(const std::vector<LevelPlan>& P) {
+  size_t b = 0;
+  const int n = (int)P.size();
+  for (int l = 0; l < n; ++l) {
+    const LevelPlan& L = P[l];
+    const int64_t nm = L.n_cells * L.nmetric * L.nloc;
+    b += bytes_of<double>(L.n_vertices * L.dim) + bytes_of<int32_t>(L.n_cells << L.dim) +
+         bytes_of<int32_t>(L.n_cells * L.nloc) + 2 * bytes_of<int32_t>(L.n_nodes) +
+         bytes_of<uint8_t>(L.rows) + bytes_of<double>(nm) + bytes_of<float>(nm) +
+         bytes_of<double>(L.n_nodes * L.dim) + 2 * bytes_of<double>(L.rows) + bytes_of<float>(L.rows);
+    if (l >= 1) {
+      const int64_t np = L.n_free_nodes;
+      b += bytes_of<int32_t>(np) + bytes_of<double>(np * L.dim) + bytes_of<float>(np * L.dim) +
+           bytes_of<int32_t>(P[l - 1].n_cells + 1);
+    }
+    if (l + 1 < n) b += bytes_of<int32_t>(L.n_nodes + 1) + bytes_of<int32_t>(L.gather_entries);
+  }
+  const int64_t nfr = P[0].n_free_nodes * P[0].ncomp;
+  b += bytes_of<int32_t>(nfr);
+  if (nfr > 0)
+    b += bytes_of<double>(nfr * nfr) + bytes_of<double>((int64_t)kCoarseMaxSegments * nfr * kMaxRhs);
+  return b;
+}
+
+// Device bytes the work buffers of solves with nrhs columns add (V-cycle
+// vectors and cell buffers in both precisions, PCG vectors).
+size_t planned_solve_bytes(const std::vector<LevelPlan>& P, int nrhs) {
+  size_t b = 0;
+  for (size_t l = 0; l < P.size(); ++l) {
+    const LevelPlan& L = P[l];
+    size_t per = (size_t)L.rows * nrhs * (l ? 4 : 2);
+    if (l) per += (size_t)P[l - 1].n_cells * P[l - 1].nloc * L.ncomp * nrhs;
+    b += per * (sizeof(float) + sizeof(double));
+  }
+  b += (size_t)P.back().rows * nrhs * (5 * sizeof(double) + sizeof(float));
+  return b;
+}
+}  // namespace
 
 // ====================================================================== C ABI
 extern "C" {
@@ -891,6 +972,11 @@ int nnmg_setup_hierarchy(const nnmg_level_desc* levels, int n_levels, const nnmg
     }
     h->lv.resize(n_levels);
     int rc = NNMG_OK;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+      set_error("cudaGetDevice failed");
+      rc = NNMG_CUDA_ERROR;
+    }
+    if (rc == NNMG_OK) rc = noalloc_scratch_lookup(&h->noalloc_scratch);
     for (int l = 0; l < n_levels && rc == NNMG_OK; ++l) rc = setup_level(h, levels[l], h->lv[l], s);
     double t = wall_seconds();
     for (int l = 1; l < n_levels && rc == NNMG_OK; ++l) rc = setup_transfer(h, l, s);
@@ -950,17 +1036,51 @@ int nnmg_level_info(const nnmg_handle* h, int level, int64_t* n_nodes, int64_t* 
 
 size_t nnmg_hierarchy_bytes(const nnmg_handle* h) { return h ? h->bytes : 0; }
 
+int nnmg_estimate_bytes(const nnmg_level_desc* levels, int n_levels, const nnmg_options* opt,
+                        int nrhs, size_t* hierarchy_bytes, size_t* solve_bytes) {
+  set_error("");
+  if (!levels || !opt || n_levels < 1 || nrhs < 1 || nrhs > kMaxRhs || opt->degree < 1 ||
+      opt->degree > kMaxDegree || (opt->n_components != 1 && opt->n_components != 3)) {
+    set_error("nnmg_estimate_bytes: bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  try {
+    std::vector<HostNumbering> num((size_t)n_levels);
+    std::vector<LevelPlan> plan((size_t)n_levels);
+    for (int l = 0; l < n_levels; ++l) {
+      const nnmg_level_desc& d = levels[l];
+      if ((d.dim != 2 && d.dim != 3) || d.n_cells < 1 || d.n_vertices < 1 || !d.cells ||
+          d.degree < 0 || d.degree > kMaxDegree) {
+        set_error("nnmg_estimate_bytes: invalid level description");
+        return NNMG_INVALID_ARG;
+      }
+      for (int64_t i = 0; i < d.n_cells * (1 << d.dim); ++i)
+        if (d.cells[i] < 0 || d.cells[i] >= d.n_vertices) {
+          set_error("nnmg_estimate_bytes: cell vertex index out of range");
+          return NNMG_INVALID_ARG;
+        }
+      const int k = d.degree > 0 ? d.degree : opt->degree;
+      int rc = number_nodes(d.cells, d.n_cells, d.n_vertices, d.dim, k, d.dirichlet_vertex, &num[l]);
+      if (rc != NNMG_OK) return rc;
+      plan[l] = level_plan(d.dim, k, opt->n_components, d.n_vertices, d.n_cells, num[l]);
+    }
+    if (hierarchy_bytes) *hierarchy_bytes = planned_hierarchy_bytes(plan);
+    if (solve_bytes) *solve_bytes = planned_solve_bytes(plan, nrhs);
+    return NNMG_OK;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return NNMG_OUT_OF_MEMORY;
+  }
+}
+
 size_t nnmg_solve_bytes(const nnmg_handle* h, int nrhs) {
   if (!h) return 0;
-  size_t b = 0;
+  std::vector<LevelPlan> plan(h->lv.size());
   for (size_t l = 0; l < h->lv.size(); ++l) {
     const DevLevel& L = h->lv[l];
-    size_t per = (size_t)L.rows * nrhs * (l ? 4 : 2);
-    if (l) per += (size_t)h->lv[l - 1].n_cells * h->lv[l - 1].nloc * L.ncomp * nrhs;
-    b += per * (sizeof(float) + sizeof(double));
+    plan[l] = level_plan(L.dim, L.k, L.ncomp, L.n_vertices, L.n_cells, L.num);
   }
-  b += (size_t)h->lv.back().rows * nrhs * (5 * sizeof(double) + sizeof(float));
-  return b;
+  return planned_solve_bytes(plan, nrhs);
 }
 
 int nnmg_support_points(const nnmg_handle* h, int level, double* pts) {

@@ -65,12 +65,8 @@ def nnmg_default_options():
     return o
 
 
-def nnmg_setup_hierarchy(levels, degree, n_components=1, lame=(1.0, 1.0), cheb_degree=3,
-                         smoothing_range=20.0, lanczos_steps=12, eig_safety=1.2, max_nrhs=16,
-                         stream=None, level_degrees=None):
-    """levels: sequence with .dim, .vertices [nv,dim] f64, .cells [nc,2^dim] i32, .dirichlet [nv] u8.
-
-    level_degrees: optional per-level degrees (0 = `degree`), coarse -> fine."""
+def _descs_and_options(levels, degree, n_components, lame, cheb_degree, smoothing_range,
+                       lanczos_steps, eig_safety, max_nrhs, level_degrees):
     keep = []
     descs = (_abi.LevelDesc * len(levels))()
     for i, lv in enumerate(levels):
@@ -86,10 +82,40 @@ def nnmg_setup_hierarchy(levels, degree, n_components=1, lame=(1.0, 1.0), cheb_d
     o.lam, o.mu = float(lame[0]), float(lame[1])
     o.cheb_degree, o.smoothing_range = int(cheb_degree), float(smoothing_range)
     o.lanczos_steps, o.eig_safety, o.max_nrhs = int(lanczos_steps), float(eig_safety), int(max_nrhs)
+    return descs, o, keep
+
+
+def nnmg_setup_hierarchy(levels, degree, n_components=1, lame=(1.0, 1.0), cheb_degree=3,
+                         smoothing_range=20.0, lanczos_steps=12, eig_safety=1.2, max_nrhs=16,
+                         stream=None, level_degrees=None):
+    """levels: sequence with .dim, .vertices [nv,dim] f64, .cells [nc,2^dim] i32, .dirichlet [nv] u8.
+
+    level_degrees: optional per-level degrees (0 = `degree`), coarse -> fine."""
+    descs, o, keep = _descs_and_options(levels, degree, n_components, lame, cheb_degree,
+                                        smoothing_range, lanczos_steps, eig_safety, max_nrhs,
+                                        level_degrees)
     h = C.c_void_p()
     _check(_lib.nnmg_setup_hierarchy(descs, len(levels), C.byref(o), _stream(stream), C.byref(h)),
            "nnmg_setup_hierarchy")
+    del keep
     return h
+
+
+def nnmg_estimate_bytes(levels, degree, n_components=1, nrhs=16, level_degrees=None, **kw):
+    """(hierarchy bytes, solve bytes for nrhs columns) before anything is built
+    (host only: no CUDA call)."""
+    opts = dict(lame=(1.0, 1.0), cheb_degree=3, smoothing_range=20.0, lanczos_steps=12,
+                eig_safety=1.2, max_nrhs=16)
+    opts.update(kw)
+    descs, o, keep = _descs_and_options(levels, degree, n_components, opts["lame"],
+                                        opts["cheb_degree"], opts["smoothing_range"],
+                                        opts["lanczos_steps"], opts["eig_safety"],
+                                        opts["max_nrhs"], level_degrees)
+    hb, sb = C.c_size_t(), C.c_size_t()
+    _check(_lib.nnmg_estimate_bytes(descs, len(levels), C.byref(o), int(nrhs), C.byref(hb),
+                                    C.byref(sb)), "nnmg_estimate_bytes")
+    del keep
+    return hb.value, sb.value
 
 
 def nnmg_destroy(h):

@@ -7,8 +7,10 @@ retires the columns that converged, returns finished requests and admits
 queued requests into the freed slots, so requests that arrive while others are
 being solved join the running solve (iteration-level batching).  Engines of
 different families step concurrently on their own streams.  A family is built
-only if its device bytes fit the memory budget; idle families are evicted
-(least recently used) to make room.
+only if its device bytes fit the memory budget; the bytes are known before
+anything is allocated (nnmg_estimate_bytes numbers the meshes on the host), so
+a family that does not fit waits without touching device memory, and idle
+families are evicted (least recently used) to make room.
 
 The scheduler is host code; every arithmetic step runs in libnnmg's kernels.
 """
@@ -90,6 +92,14 @@ class FamilyEngine:
 
     def bytes(self):
         return self.H.hierarchy_bytes() + self.H.solve_bytes(self.nslots)
+
+    @staticmethod
+    def estimate_bytes(name, spec, nslots=16, **kw):
+        """Device bytes of the engine, computed on the host before it is built."""
+        hb, sb = _nnmg.nnmg_estimate_bytes(spec.levels, spec.degree, spec.n_components,
+                                           nrhs=nslots, lame=spec.lame, cheb_degree=spec.cheb,
+                                           max_nrhs=nslots)
+        return hb + sb
 
     def _chk(self, st, what):
         if st != 0:
@@ -173,36 +183,43 @@ class Server:
         self.kw = dict(nslots=nslots, mode=mode, rtol=rtol, maxit=maxit)
         self.engines: dict[str, FamilyEngine] = {}
         self.evictions = 0
+        self.builds = 0
+        self._sizes: dict[str, int] = {}
         # builds a family's engine: FamilyEngine unless a caller substitutes
-        # its own (same constructor arguments, bytes(), busy(), close(),
-        # last_used)
+        # its own (same constructor arguments, estimate_bytes(), bytes(),
+        # busy(), close(), last_used)
         self._make = engine_factory or FamilyEngine
 
     def used_bytes(self):
         return sum(e.bytes() for e in self.engines.values())
 
+    def family_bytes(self, name):
+        """Device bytes of a family's engine, known before it is built (cached)."""
+        if name not in self._sizes:
+            self._sizes[name] = self._make.estimate_bytes(name, self.families[name], **self.kw)
+        return self._sizes[name]
+
     def engine(self, name):
-        """The family's engine, building it if the budget allows (evicting idle ones)."""
+        """The family's engine, building it if the budget allows (evicting idle
+        ones first); None if it has to wait for a busy engine to become idle.
+        Nothing is allocated for a family that waits."""
         if name in self.engines:
             return self.engines[name]
-        eng = None
-        while True:
+        need = self.family_bytes(name)
+        if need > self.budget:
+            raise MemoryError(f"family {name} needs {need} bytes, budget {self.budget}")
+        while self.used_bytes() + need > self.budget:
             idle = [e for e in self.engines.values() if not e.busy()]
-            if eng is None:
-                eng = self._make(name, self.families[name], **self.kw)
-            if self.used_bytes() + eng.bytes() <= self.budget:
-                self.engines[name] = eng
-                return eng
             if not idle:
-                need = eng.bytes()
-                eng.close()
-                if not self.engines:
-                    raise MemoryError(f"family {name} needs {need} bytes, budget {self.budget}")
                 return None       # wait until an engine becomes idle
             victim = min(idle, key=lambda e: e.last_used)
             victim.close()
             del self.engines[victim.name]
             self.evictions += 1
+        eng = self._make(name, self.families[name], **self.kw)
+        self.builds += 1
+        self.engines[name] = eng
+        return eng
 
     def prepare(self, names):
         for n in names:
@@ -241,11 +258,17 @@ class Server:
                     eng.admit(time.perf_counter() - t0)
                     eng.step()
             if not progressed:
+                # wait for the next event: a step finishing on the GPU (polled
+                # without sleeping while steps are in flight) or, with nothing
+                # in flight, the next arrival
                 inflight = [e for e in self.engines.values() if e.inflight]
                 if inflight and not pending and not waiting:
                     inflight[0].stream.synchronize()
-                else:
-                    time.sleep(0.0002)
+                elif not inflight and pending and not waiting and \
+                        not any(e.busy() for e in self.engines.values()):
+                    dt = pending[0].arrival * time_scale - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
         torch.cuda.synchronize()
         return finished
 

@@ -59,3 +59,32 @@ def test_profile_columns_match_header():
     assert sorted(idx) == sorted(names)
     for k, i in idx.items():
         assert _abi.PROF_COLUMNS[i] == names[k], k
+
+
+def test_size_estimate_runs_on_the_host():
+    """nnmg_estimate_bytes needs no GPU (it numbers the meshes on the host):
+    its solve bytes follow from the node counts of the oracle's independent
+    numbering, and bad arguments are rejected."""
+    import numpy as np
+    from oracle import dofs
+    from paper_2412_10910_gb300 import nnmg
+    from synthetic import config_levels
+    levels = config_levels("c1_2d_q1")
+    k, nrhs = 2, 4
+    hb, sb = nnmg.nnmg_estimate_bytes(levels, k, 1, nrhs=nrhs)
+    counts = []
+    for lv in levels:
+        node_of, nn, _, _ = dofs.number_dofs(lv.cells, k, 2)
+        counts.append((nn, lv.cells.shape[0]))
+    # V-cycle vectors (f, x on every level; t, d and the cell buffer above the
+    # coarsest) in FP32 and FP64, plus six PCG vectors (five FP64, one FP32)
+    expect = 0
+    for l, (nn, nc) in enumerate(counts):
+        per = nn * nrhs * (4 if l else 2) + (counts[l - 1][1] * (k + 1) ** 2 * nrhs if l else 0)
+        expect += per * 12
+    expect += counts[-1][0] * nrhs * (5 * 8 + 4)
+    assert sb == expect
+    nc_top = counts[-1][1]
+    assert hb > nc_top * 3 * (k + 1) ** 2 * 12          # FP64 + FP32 metric terms of the top level
+    with np.testing.assert_raises(nnmg.NNMGError):
+        nnmg.nnmg_estimate_bytes(levels, 7, 1)

@@ -119,9 +119,17 @@ def test_vcycle(case):
     z = H.vector(top, nrhs)
     H.vcycle(torch.tensor(r, device="cuda"), z)
     assert _relmax(z.cpu().numpy(), zo) <= 1e-9
+    # FP32 V-cycle against the oracle's V-cycle run in float arithmetic (the same
+    # Algorithm 1 on float CSR matrices).  The two round differently; on these
+    # cases the oracle's FP32 and FP64 V-cycles differ by 1e-7 .. 2e-6 relative
+    # max-norm, so both distances are held to the FP32 apply tolerance.
+    r32 = torch.tensor(r, dtype=torch.float32, device="cuda")
+    zo32 = O.vcycle(r32.double().cpu().numpy(), "fp32")
     z32 = H.vector(top, nrhs, torch.float32)
-    H.vcycle(torch.tensor(r, dtype=torch.float32, device="cuda"), z32)
-    assert _relmax(z32.double().cpu().numpy(), zo) <= 1e-3
+    H.vcycle(r32, z32)
+    z32 = z32.double().cpu().numpy()
+    assert _relmax(z32, zo32) <= 2e-5, _relmax(z32, zo32)
+    assert _relmax(z32, zo) <= 2e-5, _relmax(z32, zo)
     z2 = H.vector(top, nrhs)                   # second call replays the captured graph
     H.vcycle(torch.tensor(r, device="cuda"), z2)
     assert _relmax(z2.cpu().numpy(), zo) <= 1e-9

@@ -74,3 +74,47 @@ def test_each_result_same_alone_and_in_the_mix(budget_gb):
     st = latency_stats(done)
     assert st["p99_s"] >= st["p50_s"] > 0
     server.close()
+
+
+def test_size_estimate_equals_built_bytes():
+    """nnmg_estimate_bytes (host only, before setup) equals what the built
+    hierarchy reports, for Poisson, elasticity and polynomial-coarsening
+    hierarchies."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_10910_gb300 import nnmg
+    cases = [(config_levels("c1_2d_q1"), 2, 1, None),
+             (family_levels(3, 19, 3, 0.15, 40), 1, 1, None),
+             (config_levels("c4_3d_q2_elasticity", n_levels=2), 2, 3, None),
+             ([config_levels("c2_3d_q2", n_levels=1)[0]] + config_levels("c2_3d_q2", n_levels=2),
+              2, 1, [1, 2, 2])]
+    for levels, k, nc, degs in cases:
+        for nrhs in (1, 16):
+            hb, sb = nnmg.nnmg_estimate_bytes(levels, k, nc, nrhs=nrhs, level_degrees=degs)
+            H = nnmg.Hierarchy(levels, k, nc, level_degrees=degs)
+            assert (hb, sb) == (H.hierarchy_bytes(), H.solve_bytes(nrhs))
+            H.close()
+
+
+def test_a_waiting_family_allocates_nothing():
+    """Budget for one family at a time, the built one busy: the other family
+    waits, is not built, and device free memory does not change."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_10910_gb300.serving import FamilyEngine, Server
+    fams = _families()
+    sizes = {n: FamilyEngine.estimate_bytes(n, s) for n, s in fams.items()}
+    a, b = sorted(sizes, key=sizes.get)[:2]
+    server = Server(fams, budget_bytes=sizes[a] + sizes[b] - 1)
+    ea = server.engine(a)
+    ea.queue.append(None)                     # a queued request keeps it busy
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert server.engine(b) is None
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert server.builds == 1 and list(server.engines) == [a]
+    ea.queue.clear()
+    assert server.engine(b) is not None and server.evictions == 1
+    server.close()

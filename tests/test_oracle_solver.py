@@ -34,6 +34,33 @@ def test_chebyshev_error_reduction_is_closed_form(m):
     np.testing.assert_allclose((xs - x) / (xs - x0), _cheb_poly(m, lam, a, b), atol=1e-12)
 
 
+@pytest.mark.parametrize("m", [1, 3, 5])
+def test_chebyshev_with_jacobi_scaling_is_closed_form(m):
+    """Non-identity diagonal: A = D^(1/2) Q diag(lam) Q^T D^(1/2) with a random
+    orthogonal Q, so D^-1 A has eigenvalues lam and eigenvectors D^(-1/2) Q.
+    The error of m Chebyshev steps for D^-1 A, written in that eigenbasis
+    (coefficients Q^T D^(1/2) e), shrinks by T_m((theta-lam)/delta)/T_m(theta/delta)
+    per component (Sec. 4: Chebyshev around point Jacobi).  Passing D where D^-1
+    belongs, or dropping the scaling, changes the spectrum the polynomial acts on
+    (the diagonal spans two decades here) and fails this."""
+    rng = np.random.default_rng(m)
+    n = 30
+    lam = np.linspace(0.05, 2.0, n)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    dg = 10.0 ** rng.uniform(-1, 1, n)
+    sq = np.sqrt(dg)
+    A = sp.csr_matrix(sq[:, None] * (Q * lam) @ Q.T * sq[None, :])
+    a, b = 0.1, 1.8
+    xs = rng.standard_normal(n)
+    f = A @ xs
+    coeff = lambda e: Q.T @ (sq * e)
+    x = multigrid.chebyshev(A, 1.0 / dg, f, None, m, a, b, x_is_zero=True)
+    np.testing.assert_allclose(coeff(xs - x) / coeff(xs), _cheb_poly(m, lam, a, b), atol=1e-10)
+    x0 = rng.standard_normal(n)
+    x = multigrid.chebyshev(A, 1.0 / dg, f, x0, m, a, b, x_is_zero=False)
+    np.testing.assert_allclose(coeff(xs - x) / coeff(xs - x0), _cheb_poly(m, lam, a, b), atol=1e-10)
+
+
 def test_lanczos_exact_when_steps_exceed_dimension():
     rng = np.random.default_rng(0)
     B = rng.standard_normal((9, 9))

@@ -1,8 +1,9 @@
 """Host logic of the serving loop: families are built under a device-memory
 budget, idle families are evicted least recently used first, a family that
-does not fit waits while every built family is busy, and a family larger
-than the whole budget is an error.  The engines are stand-ins with the
-interface the server uses (bytes, busy, close, last_used), so no GPU work is
+does not fit waits while every built family is busy (and is not built while
+it waits: its size is known beforehand), and a family larger than the whole
+budget is an error.  The engines are stand-ins with the interface the server
+uses (estimate_bytes, bytes, busy, close, last_used), so no GPU work is
 involved."""
 import pytest
 
@@ -12,8 +13,14 @@ from paper_2412_10910_gb300.serving import Server
 class FakeEngine:
     sizes = {}
     clock = [0.0]
+    built = []
+
+    @staticmethod
+    def estimate_bytes(name, spec, **kw):
+        return FakeEngine.sizes[name]
 
     def __init__(self, name, spec, **kw):
+        FakeEngine.built.append(name)
         self.name = name
         self.kw = kw
         self.is_busy = False
@@ -33,6 +40,7 @@ class FakeEngine:
 
 def _server(sizes, budget):
     FakeEngine.sizes = dict(sizes)
+    FakeEngine.built = []
     return Server({n: None for n in sizes}, budget_bytes=budget, engine_factory=FakeEngine)
 
 
@@ -52,8 +60,10 @@ def test_busy_families_are_not_evicted_and_the_newcomer_waits():
     s = _server({"a": 60, "b": 60}, 100)
     a = s.engine("a")
     a.is_busy = True
-    assert s.engine("b") is None                   # must wait, nothing evicted
+    for _ in range(5):
+        assert s.engine("b") is None               # must wait, nothing evicted
     assert not a.closed and s.evictions == 0 and list(s.engines) == ["a"]
+    assert FakeEngine.built == ["a"] and s.builds == 1   # "b" never built while it waits
     a.is_busy = False
     b = s.engine("b")
     assert b is not None and a.closed and s.evictions == 1
@@ -63,6 +73,7 @@ def test_a_family_larger_than_the_budget_is_an_error():
     s = _server({"big": 500}, 100)
     with pytest.raises(MemoryError):
         s.engine("big")
+    assert FakeEngine.built == []                  # rejected before anything is built
 
 
 def test_server_passes_the_solver_settings_to_its_engines():
