@@ -39,11 +39,17 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_PIPE_TOPS = 152 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
-# fine-level operator on this workload, for the kernel choice the counters
-# were taken on (404.5 + 65.5 MB, op_reg_kernel<3,2,double>); reported only
-# when the autotuner picks that kernel.
-OP64_TRAFFIC = {-1: 470.0e6}
+# DRAM bytes per (cell, right-hand side) of the FP64 fine-level operator, from
+# ncu's dram__bytes_read.sum + dram__bytes_write.sum of one launch on config 2
+# (404.5 + 65.5 MB over 166,375 cells x 8 RHS), keyed by the kernel choice
+# the counters were taken on (-1: op_reg_kernel<3,2,double>).  The launch's
+# traffic is this times its cells x RHS; another choice reports null.
+OP64_TRAFFIC_PER_UNIT = {-1: 470.0e6 / (166375 * 8)}
+
+
+def op64_traffic(choice, n_cells, nrhs):
+    per = OP64_TRAFFIC_PER_UNIT.get(choice)
+    return None if per is None else per * n_cells * nrhs
 
 
 def poisson3d_work(n):
@@ -492,6 +498,39 @@ def run_serving(args, rank):
     server.close()
 
 
+# FMA-chain iterations per probe launch (about 50 ms each on GB300)
+PROBE_ITERS = {0: 4000, 1: 200000, 2: 100000}
+
+
+def pipe_rates(reps=3):
+    """Best of `reps` FMA-chain probe launches per pipe (nnmg_pipe_rate), in
+    multiply-adds per second: FP64 (DFMA), FP32 (FFMA), packed FP32 (FFMA2)."""
+    from paper_2412_10910_gb300 import nnmg
+    return {name: max(nnmg.nnmg_pipe_rate(kind, PROBE_ITERS[kind]) for _ in range(reps))
+            for kind, name in ((0, "fp64"), (1, "fp32"), (2, "fp32_packed"))}
+
+
+def run_peaks(args, rank):
+    """The arithmetic pipe rates of this GPU (the ALU rooflines' denominators),
+    with the SM clock sampled while the probes run: rate / (SMs x median clock)
+    gives the multiply-adds per clock and SM the pipe sustains."""
+    import torch
+    clocks = Clocks()
+    clocks.start()
+    rates = pipe_rates(reps=max(3, args.steps))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clk.get("sm_mhz") or 2070.0
+    per_clk = {k: v / (sms * mhz * 1e6) for k, v in rates.items()}
+    if rank == 0:
+        print(json.dumps({"only": "peaks", "fma_per_s": rates, "sms": sms,
+                          "fma_per_clock_per_sm": per_clk, "clocks": clk,
+                          "fp64_tflops": 2 * rates["fp64"] / 1e12,
+                          "fp32_tflops": 2 * max(rates["fp32"], rates["fp32_packed"]) / 1e12}),
+              flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,7 +539,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["solve", "solve64", "solvedw", "vcycle", "op64", "op32",
-                                       "opdw", "serving", "configs"],
+                                       "opdw", "serving", "configs", "peaks"],
                     default=None, help="run only one timed section (for profiler launch lists), "
                     "or the serving mix")
     ap.add_argument("--requests", type=int, default=2000, help="serving mix: number of requests")
@@ -523,6 +562,8 @@ def main():
     from synthetic.meshes import CONFIGS
 
     torch.cuda.set_device(local)
+    if args.only == "peaks":
+        return run_peaks(args, rank)
     if args.only == "serving":
         return run_serving(args, rank)
     if args.only == "configs":
@@ -676,7 +717,10 @@ def main():
     barrier()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / ke)
 
-    # ---- roofline of the dominant kernel: the FP64 fine-level operator (ALU bound)
+    # ---- roofline of the dominant kernel: the FP64 fine-level operator (ALU bound),
+    # against the FP64 pipe rate measured now by the FMA-chain probe
+    rates = pipe_rates(reps=3)
+    fp64_peak = rates["fp64"] / 1e12
     flops_cell, ops_cell = poisson3d_work(cfg["degree"] + 1)
     flops = float(flops_cell) * n_cells * nrhs
     op64_ms = statistics.mean(top64)
@@ -710,14 +754,18 @@ def main():
         # (flops beside it: an ADD is one flop in a full slot).
         "roofline": {"kernel": operator_kernel_name(choice64, cfg["degree"], "double")
                      + ", FP64 fine-level operator, 8 RHS",
-                     "bound": "alu", "achieved": pipe, "peak": FP64_PIPE_TOPS,
-                     "unit": "T FP64-pipe op/s (FMA, MUL or ADD)", "frac": pipe / FP64_PIPE_TOPS,
+                     "bound": "alu", "achieved": pipe, "peak": fp64_peak,
+                     "unit": "T FP64-pipe op/s (FMA, MUL or ADD)", "frac": pipe / fp64_peak,
                      "ops_per_cell_rhs": ops_cell, "flops_per_cell_rhs": flops_cell,
-                     "achieved_tflops": achieved, "peak_tflops": FP64_PEAK_TFLOPS,
-                     # DRAM bytes read + written per launch, ncu capture of this kernel
-                     "traffic": OP64_TRAFFIC.get(choice64),
-                     "peak_source": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz "
-                                    "(an FMA-chain probe reached 0.596 T/s = 0.95 of it)"},
+                     "achieved_tflops": achieved, "peak_tflops": 2 * fp64_peak,
+                     "nominal_peak": FP64_PIPE_TOPS, "frac_of_nominal": pipe / FP64_PIPE_TOPS,
+                     # DRAM bytes read + written per launch: ncu's bytes per (cell, RHS)
+                     # for this kernel on this workload, times the launch's cells x RHS
+                     "traffic": op64_traffic(choice64, n_cells, nrhs),
+                     "peak_source": "measured in this run: FMA-chain probe (nnmg_pipe_rate, "
+                                    "best of 3, DFMA chains on every SM); nominal "
+                                    "152 SM x 2 FP64 op/clk x 2.07 GHz beside it"},
+        "pipe_rates_fma_per_s": rates,
         # FP32 V-cycle per level and component (ms, event-timed eager run) and the
         # fine level's kernels against the measured HBM copy bandwidth
         "vcycle_breakdown_ms": breakdown,

@@ -337,6 +337,16 @@ int nnmg_batch_poll(nnmg_handle* h, int wait, int* ready, int* active, int* iter
                     double* relres, int* status);
 int nnmg_batch_retire(nnmg_handle* h, int slot, double* x, int x_on_host, void* stream);
 
+/* Arithmetic pipe rate of the current GPU (no counterpart in the paper: the
+ * denominator of the rooflines of ALU-bound kernels).  Runs independent
+ * fused multiply-add chains on every SM (8 per thread, 2048 threads per SM,
+ * no memory traffic) for `iters` x 32 steps per chain, once to warm up and
+ * once timed with CUDA events on `stream`; *fma_per_s = multiply-adds per
+ * second.  kind: 0 FP64 (DFMA), 1 FP32 (FFMA), 2 packed FP32 pairs (FFMA2,
+ * two multiply-adds per instruction).  Allocates a small device buffer.
+ * Errors: INVALID_ARG, CUDA_ERROR. */
+int nnmg_pipe_rate(int kind, int iters, void* stream, double* fma_per_s);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* nnmg_last_error(void);
 

@@ -113,6 +113,7 @@ struct DevLevel {
   // transfer from the next coarser level (this level is the fine one), l >= 1
   int64_t n_pts = 0;
   int32_t* pt_node = nullptr;        // [n_pts] fine node, sorted by coarse cell
+  int32_t* pt_cell = nullptr;        // [n_pts] its coarse cell
   double* pt_xi64 = nullptr;         // [n_pts][dim]
   float* pt_xi32 = nullptr;
   int32_t* cell_pt_start = nullptr;  // [n_cells(coarse)+1]
@@ -164,6 +165,18 @@ cudaError_t launch_prolongate_add(const DevLevel& fine, const DevLevel& coarse, 
 template <typename T>
 cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const T* rf, T* rc,
                             T* scratch, int nrhs, cudaStream_t s);
+// The non-nested transfer's kernels (k_prolong.cu, k_restrict.cu): x_f += P x_c;
+// phase one of r_c = P^T r_f into the cell-local buffer [coarse cells][(k+1)^d]
+// [ncomp * nrhs]; phase two, the fixed-order gather of that buffer into r_c.
+template <typename T>
+cudaError_t launch_prolongate_points(const DevLevel& fine, const DevLevel& coarse, const T* xc,
+                                     T* xf, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict_points(const DevLevel& fine, const DevLevel& coarse, const T* rf,
+                                   T* scratch, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict_gather(const DevLevel& coarse, const T* scratch, T* rc, int nch,
+                                   cudaStream_t s);
 template <typename TI, typename TO>
 cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs, cudaStream_t s);
 

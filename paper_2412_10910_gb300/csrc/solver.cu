@@ -756,23 +756,26 @@ int setup_transfer(nnmg_handle* h, int fi, cudaStream_t s) {
   for (int64_t p = 0; p < np; ++p) start[F.h_loc_cell[p] + 1]++;
   for (int64_t c = 0; c < C.n_cells; ++c) start[c + 1] += start[c];
   std::vector<int32_t> fill(start.begin(), start.end() - 1);
-  std::vector<int32_t> snode((size_t)np);
+  std::vector<int32_t> snode((size_t)np), scell((size_t)np);
   std::vector<double> sxi((size_t)np * dim);
   std::vector<float> sxi32((size_t)np * dim);
   for (int64_t p = 0; p < np; ++p) {
     const int32_t q = fill[F.h_loc_cell[p]]++;
     snode[q] = pts[p];
+    scell[q] = F.h_loc_cell[p];
     for (int d = 0; d < dim; ++d) {
       sxi[(size_t)q * dim + d] = F.h_loc_xi[(size_t)p * dim + d];
       sxi32[(size_t)q * dim + d] = (float)F.h_loc_xi[(size_t)p * dim + d];
     }
   }
   CK(dalloc(h, &F.pt_node, (size_t)np));
+  CK(dalloc(h, &F.pt_cell, (size_t)np));
   CK(dalloc(h, &F.pt_xi64, (size_t)np * dim));
   CK(dalloc(h, &F.pt_xi32, (size_t)np * dim));
   CK(dalloc(h, &F.cell_pt_start, start.size()));
   if (np) {
     CK(cudaMemcpy(F.pt_node, snode.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(F.pt_cell, scell.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.pt_xi64, sxi.data(), np * dim * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(F.pt_xi32, sxi32.data(), np * dim * sizeof(float), cudaMemcpyHostToDevice));
   }
@@ -892,7 +895,7 @@ size_t planned_hierarchy_bytes(const std::vector<LevelPlan>& P) {
          bytes_of<double>(L.n_nodes * L.dim) + 2 * bytes_of<double>(L.rows) + bytes_of<float>(L.rows);
     if (l >= 1) {
       const int64_t np = L.n_free_nodes;
-      b += bytes_of<int32_t>(np) + bytes_of<double>(np * L.dim) + bytes_of<float>(np * L.dim) +
+      b += 2 * bytes_of<int32_t>(np) + bytes_of<double>(np * L.dim) + bytes_of<float>(np * L.dim) +
            bytes_of<int32_t>(P[l - 1].n_cells + 1);
     }
     if (l + 1 < n) b += bytes_of<int32_t>(L.n_nodes + 1) + bytes_of<int32_t>(L.gather_entries);

@@ -331,6 +331,14 @@ def nnmg_pcg_solve_host(h, mode, b, x, nrhs, rtol=1e-8, maxit=200, stream=None, 
     return st, its, rel
 
 
+def nnmg_pipe_rate(kind, iters=20000, stream=None):
+    """Fused multiply-adds per second of the FP64 (kind 0), FP32 (1) or packed
+    FP32 (2) pipe, from an FMA-chain kernel timed with CUDA events."""
+    r = C.c_double()
+    _check(_lib.nnmg_pipe_rate(int(kind), int(iters), _stream(stream), C.byref(r)), "nnmg_pipe_rate")
+    return r.value
+
+
 def nnmg_last_error():
     return _lib.nnmg_last_error().decode(errors="replace")
 
