@@ -276,8 +276,11 @@ int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
  * NNMG_PROF_POST are the six components (the coarse solve on level 0, the
  * others on levels >= 1; restriction and prolongation are booked on the fine
  * level of their pair), NNMG_PROF_OPERATOR and NNMG_PROF_VECTOR the same
- * launches by kernel class (operator applications; Chebyshev and residual
- * vector updates).  launches (host, same shape, may be NULL): how many
+ * launches by kernel class (operator applications; Chebyshev vector
+ * updates).  The residual r_l = f_l - A_l x_l is formed inside the
+ * restriction's first kernel, so the residual column holds the operator
+ * application A_l x_l and the restrictor column the subtraction with the
+ * transfer.  launches (host, same shape, may be NULL): how many
  * launches each entry sums.  Event timing adds a few microseconds per launch
  * on small levels.  INVALID_ARG for bad arguments or when called inside a
  * stream capture. */

@@ -43,9 +43,9 @@ constexpr int kStagePts = 32 * kLanePts;
 // which shares each loaded factor and product over more entries (3D Q3/Q4).
 template <int D, int K, typename T, int CH, int F>
 __global__ void __launch_bounds__(128, F == 1 ? NNMG_RESTRICT_MIN_BLOCKS : 4) restrict_pts_kernel(
-    const T* __restrict__ rf, T* __restrict__ buf, const int32_t* __restrict__ cell_pt_start,
-    const int32_t* __restrict__ pt_node, const T* __restrict__ pt_xi, int64_t n_cells, int nch,
-    Basis1D<T> B) {
+    const T* __restrict__ rf, T* __restrict__ tres, T* __restrict__ buf,
+    const int32_t* __restrict__ cell_pt_start, const int32_t* __restrict__ pt_node,
+    const T* __restrict__ pt_xi, int64_t n_cells, int nch, Basis1D<T> B) {
   constexpr int N = K + 1;
   constexpr int NL = ipow<N, D>::value;
   constexpr int NO = F == 1 ? NL / N : N;         // owned lines (i[, j]) or planes (i)
@@ -94,6 +94,24 @@ __global__ void __launch_bounds__(128, F == 1 ? NNMG_RESTRICT_MIN_BLOCKS : 4) re
 #pragma unroll
           for (int b = 0; b < kLanePts; ++b)
             if (node[b] >= 0) load_group<T, CH>(rf + (int64_t)node[b] * nch + gg * CH, v[b]);
+          if (tres) {
+            // fused residual: r = f - t at the point's row, and t = 0 there in
+            // the last round over the points (every free fine node is exactly
+            // one point, so all of t is reset; earlier rounds still read t)
+            P tv[kLanePts][NP], zero[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) zero[q] = pzero(P());
+#pragma unroll
+            for (int b = 0; b < kLanePts; ++b)
+              if (node[b] >= 0) load_group<T, CH>(tres + (int64_t)node[b] * nch + gg * CH, tv[b]);
+#pragma unroll
+            for (int b = 0; b < kLanePts; ++b)
+              if (node[b] >= 0) {
+#pragma unroll
+                for (int q = 0; q < NP; ++q) v[b][q] = psub(v[b][q], tv[b][q]);
+                if (rd == rounds - 1) store_group<T, CH>(tres + (int64_t)node[b] * nch + gg * CH, zero);
+              }
+          }
 #pragma unroll
           for (int b = 0; b < kLanePts; ++b)
             if (node[b] >= 0) store_group<T, CH>(sr + (lane + 32 * b) * nch + gg * CH, v[b]);
@@ -215,8 +233,8 @@ template <>
 const float* xi_for<float>(const DevLevel& L) { return L.pt_xi32; }
 
 template <int D, int K, typename T, int CH, int F>
-cudaError_t restrict_run(const DevLevel& f, const DevLevel& c, const T* rf, T* buf, int nch,
-                         cudaStream_t s) {
+cudaError_t restrict_run(const DevLevel& f, const DevLevel& c, const T* rf, T* tres, T* buf,
+                         int nch, cudaStream_t s) {
   constexpr int N = K + 1;
   Basis1D<T> B;
   basis_for<T>(K, &B);
@@ -232,36 +250,36 @@ cudaError_t restrict_run(const DevLevel& f, const DevLevel& c, const T* rf, T* b
     granted = smem;
   }
   const unsigned blocks = (unsigned)((c.n_cells + warps - 1) / warps);
-  kern<<<blocks, 32 * warps, smem, s>>>(rf, buf, f.cell_pt_start, f.pt_node, xi_for<T>(f),
-                                                 c.n_cells, nch, B);
+  kern<<<blocks, 32 * warps, smem, s>>>(rf, tres, buf, f.cell_pt_start, f.pt_node, xi_for<T>(f),
+                                        c.n_cells, nch, B);
   return cudaGetLastError();
 }
 
 template <int D, int K, typename T>
-cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* buf, int nch,
-                        cudaStream_t s) {
+cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* tres, T* buf,
+                        int nch, cudaStream_t s) {
   // the buffer rows are allocated by cudaMalloc or the no-allocation array
   // (256-byte aligned): only the fine vector's alignment can vary.  3D Q3/Q4
   // own planes (F = 2) of up to 25 entries, with at most 2 FP32 channels (a
   // float pair) or 1 FP64 channel per lane.
   constexpr bool planes = D == 3 && K >= 3;
-  int ch = channel_group<T>(nch, rf, buf);
+  int ch = channel_group<T>(nch, rf, tres ? (const void*)tres : (const void*)buf);
   if (planes) ch = std::min(ch, sizeof(T) == 4 ? 2 : 1);
   if constexpr (planes) {
     switch (ch) {
       case 2:
-        if constexpr (sizeof(T) == 4) return restrict_run<D, K, T, 2, 2>(f, c, rf, buf, nch, s);
+        if constexpr (sizeof(T) == 4) return restrict_run<D, K, T, 2, 2>(f, c, rf, tres, buf, nch, s);
         break;
-      default: return restrict_run<D, K, T, 1, 2>(f, c, rf, buf, nch, s);
+      default: return restrict_run<D, K, T, 1, 2>(f, c, rf, tres, buf, nch, s);
     }
   } else {
     switch (ch) {
       case 8:
-        if constexpr (sizeof(T) == 4) return restrict_run<D, K, T, 8, 1>(f, c, rf, buf, nch, s);
+        if constexpr (sizeof(T) == 4) return restrict_run<D, K, T, 8, 1>(f, c, rf, tres, buf, nch, s);
         break;
-      case 4: return restrict_run<D, K, T, 4, 1>(f, c, rf, buf, nch, s);
-      case 2: return restrict_run<D, K, T, 2, 1>(f, c, rf, buf, nch, s);
-      default: return restrict_run<D, K, T, 1, 1>(f, c, rf, buf, nch, s);
+      case 4: return restrict_run<D, K, T, 4, 1>(f, c, rf, tres, buf, nch, s);
+      case 2: return restrict_run<D, K, T, 2, 1>(f, c, rf, tres, buf, nch, s);
+      default: return restrict_run<D, K, T, 1, 1>(f, c, rf, tres, buf, nch, s);
     }
   }
   return cudaErrorInvalidValue;
@@ -271,13 +289,15 @@ cudaError_t restrict_dk(const DevLevel& f, const DevLevel& c, const T* rf, T* bu
 
 // Phase one of r_c = P^T r_f into the cell-local buffer `scratch`
 // [coarse cells][(k+1)^d][ncomp * nrhs] (instantiated on the coarse degree).
+// With tres != nullptr the residual is fused: r_f = rf - tres at the located
+// points, and tres is reset to zero there.
 template <typename T>
 cudaError_t launch_restrict_points(const DevLevel& fine, const DevLevel& coarse, const T* rf,
-                                   T* scratch, int nrhs, cudaStream_t s) {
+                                   T* tres, T* scratch, int nrhs, cudaStream_t s) {
   if (coarse.n_cells == 0) return cudaSuccess;
   const int nch = fine.ncomp * nrhs;
 #define NNMG_R(D, K) \
-  if (fine.dim == D && coarse.k == K) return restrict_dk<D, K, T>(fine, coarse, rf, scratch, nch, s);
+  if (fine.dim == D && coarse.k == K) return restrict_dk<D, K, T>(fine, coarse, rf, tres, scratch, nch, s);
   NNMG_R(2, 1) NNMG_R(2, 2) NNMG_R(2, 3) NNMG_R(2, 4)
   NNMG_R(3, 1) NNMG_R(3, 2) NNMG_R(3, 3) NNMG_R(3, 4)
 #undef NNMG_R
@@ -296,9 +316,10 @@ cudaError_t launch_restrict_gather(const DevLevel& coarse, const T* scratch, T* 
 }
 
 template cudaError_t launch_restrict_points<float>(const DevLevel&, const DevLevel&, const float*,
-                                                   float*, int, cudaStream_t);
+                                                   float*, float*, int, cudaStream_t);
 template cudaError_t launch_restrict_points<double>(const DevLevel&, const DevLevel&,
-                                                    const double*, double*, int, cudaStream_t);
+                                                    const double*, double*, double*, int,
+                                                    cudaStream_t);
 template cudaError_t launch_restrict_gather<float>(const DevLevel&, const float*, float*, int,
                                                    cudaStream_t);
 template cudaError_t launch_restrict_gather<double>(const DevLevel&, const double*, double*, int,

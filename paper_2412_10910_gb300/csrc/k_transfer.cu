@@ -293,9 +293,22 @@ cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const 
 #undef NNMG_G
     return cudaErrorInvalidValue;
   }
-  cudaError_t e = launch_restrict_points<T>(fine, coarse, rf, scratch, nrhs, s);
+  cudaError_t e = launch_restrict_points<T>(fine, coarse, rf, nullptr, scratch, nrhs, s);
   if (e != cudaSuccess) return e;
   return launch_restrict_gather<T>(coarse, scratch, rc, nch, s);
+}
+
+template <typename T>
+cudaError_t launch_restrict_residual(const DevLevel& fine, const DevLevel& coarse, const T* f,
+                                     T* t, T* r_tmp, T* rc, T* scratch, int nrhs, cudaStream_t s) {
+  if (fine.gc_active || coarse.n_cells == 0) {
+    cudaError_t e = launch_residual<T>(f, t, r_tmp, fine.rows, nrhs, s);
+    if (e != cudaSuccess) return e;
+    return launch_restrict<T>(fine, coarse, r_tmp, rc, scratch, nrhs, s);
+  }
+  cudaError_t e = launch_restrict_points<T>(fine, coarse, f, t, scratch, nrhs, s);
+  if (e != cudaSuccess) return e;
+  return launch_restrict_gather<T>(coarse, scratch, rc, fine.ncomp * nrhs, s);
 }
 
 template <typename TI, typename TO>
@@ -327,6 +340,12 @@ template cudaError_t launch_restrict<float>(const DevLevel&, const DevLevel&, co
                                             float*, int, cudaStream_t);
 template cudaError_t launch_restrict<double>(const DevLevel&, const DevLevel&, const double*,
                                              double*, double*, int, cudaStream_t);
+template cudaError_t launch_restrict_residual<float>(const DevLevel&, const DevLevel&, const float*,
+                                                     float*, float*, float*, float*, int,
+                                                     cudaStream_t);
+template cudaError_t launch_restrict_residual<double>(const DevLevel&, const DevLevel&,
+                                                      const double*, double*, double*, double*,
+                                                      double*, int, cudaStream_t);
 template cudaError_t launch_coarse_solve<float, float>(const DevLevel&, const float*, float*, int,
                                                       cudaStream_t);
 template cudaError_t launch_coarse_solve<double, double>(const DevLevel&, const double*, double*,

@@ -171,9 +171,17 @@ cudaError_t launch_restrict(const DevLevel& fine, const DevLevel& coarse, const 
 template <typename T>
 cudaError_t launch_prolongate_points(const DevLevel& fine, const DevLevel& coarse, const T* xc,
                                      T* xf, int nrhs, cudaStream_t s);
+// With tres != nullptr, phase one forms the residual r_f = rf - tres itself
+// and resets tres to zero at every free fine row.
 template <typename T>
 cudaError_t launch_restrict_points(const DevLevel& fine, const DevLevel& coarse, const T* rf,
-                                   T* scratch, int nrhs, cudaStream_t s);
+                                   T* tres, T* scratch, int nrhs, cudaStream_t s);
+// The residual r_l = f_l - t (t = A_l x_l) restricted to the coarse level in
+// one pass (no residual vector): rc = P^T (f - t), t reset to zero.  The
+// nested transfer forms the residual first.
+template <typename T>
+cudaError_t launch_restrict_residual(const DevLevel& fine, const DevLevel& coarse, const T* f,
+                                     T* t, T* r_tmp, T* rc, T* scratch, int nrhs, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict_gather(const DevLevel& coarse, const T* scratch, T* rc, int nch,
                                    cudaStream_t s);

@@ -316,9 +316,9 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
     }
     RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_OPERATOR,
         launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
-    RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_VECTOR, launch_residual<T>(f, t, d, L.rows, nrhs, s));
+    // r_l = f_l - A_l x_l formed inside the restriction (t reset to zero there)
     RUN(l, NNMG_PROF_RESTRICT, NNMG_PROF_RESTRICT,
-        launch_restrict<T>(L, h->lv[l - 1], d, W.f[l - 1], W.scratch[l], nrhs, s));
+        launch_restrict_residual<T>(L, h->lv[l - 1], f, t, d, W.f[l - 1], W.scratch[l], nrhs, s));
   }
   {
     const T* f0 = top == 0 ? f_top : W.f[0];

@@ -63,6 +63,11 @@ __device__ __forceinline__ double pfma(double a, double b, double c) { return fm
 __device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float pmul(float a, float b) { return a * b; }
 __device__ __forceinline__ double pmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ float psub(float a, float b) { return a - b; }
+__device__ __forceinline__ double psub(double a, double b) { return a - b; }
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float padd(float a, float b) { return a + b; }
 __device__ __forceinline__ double padd(double a, double b) { return a + b; }

@@ -84,9 +84,10 @@ def test_fine_level_kernel_bytes_by_hand():
     # operator: x read + y write at the free row, metric 6 x 8 points x 4 B and
     # 8 indices per cell
     assert by["operator"] == 2 * 1 * 2 * 4 + 8 * 8 * (6 * 4 + 4)
-    # vector kernels: 27 rows x 2 RHS x 4 B x (3 + 5 x 7 + 4) + 7 diagonal passes
-    assert by["vector"] == 27 * 2 * 4 * (3 + 5 * 7 + 4) + 7 * 27 * 4
+    # vector kernels: 27 rows x 2 RHS x 4 B x (3 + 5 x 7) + 6 diagonal passes
+    assert by["vector"] == 27 * 2 * 4 * (3 + 5 * 7) + 6 * 27 * 4
     pts = 1 * (4 + 3 * 4)
     buf = 1 * 8 * 2 * 4
-    assert by["restrictor"] == 1 * 2 * 4 + pts + 8 * 2 * 4 + 2 * buf + 8 * 4
+    # fused residual: f and t read and t reset at the one located point
+    assert by["restrictor"] == 3 * 1 * 2 * 4 + pts + 8 * 2 * 4 + 2 * buf + 8 * 4
     assert by["prolongator"] == 8 * 2 * 4 + 8 * 4 + 2 * 1 * 2 * 4 + pts
