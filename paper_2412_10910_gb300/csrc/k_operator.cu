@@ -176,6 +176,8 @@ __device__ __forceinline__ void op3d_body(const int32_t* __restrict__ cell_nodes
                                           const typename io_of<T>::type* __restrict__ x,
                                           typename io_of<T>::type* __restrict__ y, int64_t n_cells,
                                           int nrhs, int U, const Basis1D<T>& B, T lambda, T mu) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N = K + 1, N2 = N * N, NQ = N2 * N;
   constexpr int NM = NC == 1 ? 6 : 9;
   extern __shared__ unsigned char smem_raw[];
@@ -415,6 +417,8 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
                             const typename io_of<T>::type* __restrict__ x,
                             typename io_of<T>::type* __restrict__ y, int64_t n_cells, int nrhs,
                             int U, Basis1D<T> B) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N = K + 1, NQ = N * N;
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -534,6 +538,8 @@ __global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__
                                                      const typename io_of<T>::type* __restrict__ x,
                                                      typename io_of<T>::type* __restrict__ y,
                                                      int64_t n_cells, int nrhs, Basis1D<T> B) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N = K + 1;
   constexpr int NQ = D == 2 ? N * N : N * N * N;
   constexpr int NM = D == 2 ? 3 : 6;
@@ -601,6 +607,8 @@ __global__ void __launch_bounds__(128) op_reg2_kernel(const int32_t* __restrict_
                                                       const float2* __restrict__ x,
                                                       float2* __restrict__ y, int64_t n_cells,
                                                       int npair, Basis1D<f2> B) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N = K + 1;
   constexpr int NQ = D == 2 ? N * N : N * N * N;
   constexpr int NM = D == 2 ? 3 : 6;
@@ -785,9 +793,8 @@ cudaError_t run3d(const DevLevel& L, const typename metric_type<T>::type* metric
     if (e != cudaSuccess) return e;
     smem_set[which] = c.smem;
   }
-  kern<<<c.blocks, c.threads, c.smem, s>>>(L.cell_nodes, metric, x, y, L.n_cells, nrhs, c.U, B,
-                                           arith_from_double<T>(lambda), arith_from_double<T>(mu));
-  return cudaGetLastError();
+  return launch_k(kern, c.blocks, c.threads, c.smem, s, L.cell_nodes, metric, x, y, L.n_cells, nrhs,
+                  c.U, B, arith_from_double<T>(lambda), arith_from_double<T>(mu));
 }
 
 template <int K, typename T>
@@ -798,9 +805,8 @@ cudaError_t run2d(const DevLevel& L, const T* metric, const typename io_of<T>::t
   pick_basis<T>(K, &B);
   static const int max_threads = kernel_max_threads(op2d_kernel<K, T>);
   OpConfig c = op_config(N, N * N, 2, sizeof(T), L.n_cells, nrhs, max_threads, units);
-  op2d_kernel<K, T><<<c.blocks, c.threads, c.smem, s>>>(L.cell_nodes, metric, x, y, L.n_cells,
-                                                        nrhs, c.U, B);
-  return cudaGetLastError();
+  return launch_k(op2d_kernel<K, T>, c.blocks, c.threads, c.smem, s, L.cell_nodes, metric, x, y,
+                  L.n_cells, nrhs, c.U, B);
 }
 
 template <typename T>
@@ -820,9 +826,8 @@ cudaError_t run_reg(const DevLevel& L, const T* metric, const typename io_of<T>:
   Basis1D<T> B;
   pick_basis<T>(K, &B);
   const int64_t units = L.n_cells * nrhs;
-  op_reg_kernel<D, K, T><<<(unsigned)((units + 127) / 128), 128, 0, s>>>(L.cell_nodes, metric, x, y,
-                                                                         L.n_cells, nrhs, B);
-  return cudaGetLastError();
+  return launch_k(op_reg_kernel<D, K, T>, (unsigned)((units + 127) / 128), 128, 0, s, L.cell_nodes,
+                  metric, x, y, L.n_cells, nrhs, B);
 }
 
 template <int D, int K>
@@ -832,10 +837,9 @@ cudaError_t run_reg2(const DevLevel& L, const float* metric, const float* x, flo
   pick_basis<f2>(K, &B);
   const int npair = nrhs / 2;
   const int64_t units = L.n_cells * npair;
-  op_reg2_kernel<D, K><<<(unsigned)((units + 127) / 128), 128, 0, s>>>(
-      L.cell_nodes, metric, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y),
-      L.n_cells, npair, B);
-  return cudaGetLastError();
+  return launch_k(op_reg2_kernel<D, K>, (unsigned)((units + 127) / 128), 128, 0, s, L.cell_nodes,
+                  metric, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), L.n_cells,
+                  npair, B);
 }
 
 // The register-resident kernel serves Poisson cells with at most 27 (3D) or

@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(kProlongThreads, NNMG_PROLONG_MIN_BLOCKS) prol
     const int32_t* __restrict__ cell_pt_start, const int32_t* __restrict__ pt_node,
     const int32_t* __restrict__ pt_cell, const T* __restrict__ pt_xi, int64_t n_cells, int nch,
     int G, Basis1D<T> B) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N = K + 1;
   constexpr int NL = ipow<N, D>::value;
   using P = typename Pack<T, CH>::type;
@@ -185,6 +187,8 @@ __global__ void __launch_bounds__(128) prolong_cell_kernel(
     const int32_t* __restrict__ ccell_nodes, const T* __restrict__ xc, T* __restrict__ xf,
     const int32_t* __restrict__ cell_pt_start, const int32_t* __restrict__ pt_node,
     const T* __restrict__ pt_xi, int64_t n_cells, int nch, Basis1D<T> B) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N = K + 1;
   constexpr int NL = ipow<N, D>::value;
   using P = typename Pack<T, CH>::type;
@@ -300,9 +304,8 @@ cudaError_t prolong_run(const DevLevel& f, const DevLevel& c, const T* xc, T* xf
       granted_cell = smem;
     }
     const unsigned blocks = (unsigned)((c.n_cells + warps - 1) / warps);
-    kern<<<blocks, 32 * warps, smem, s>>>(c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node,
-                                          xi_for<T>(f), c.n_cells, nch, B);
-    return cudaGetLastError();
+    return launch_k(kern, blocks, 32 * warps, smem, s, c.cell_nodes, xc, xf, f.cell_pt_start,
+                    f.pt_node, xi_for<T>(f), c.n_cells, nch, B);
   }
   // cells per block: about as many points as one batched pass of the block
   // takes, and no more cells than the staging budget allows (at least one)
@@ -318,9 +321,8 @@ cudaError_t prolong_run(const DevLevel& f, const DevLevel& c, const T* xc, T* xf
     granted = smem;
   }
   const unsigned blocks = (unsigned)((c.n_cells + G - 1) / G);
-  kern<<<blocks, kProlongThreads, smem, s>>>(c.cell_nodes, xc, xf, f.cell_pt_start, f.pt_node,
-                                              f.pt_cell, xi_for<T>(f), c.n_cells, nch, G, B);
-  return cudaGetLastError();
+  return launch_k(kern, blocks, kProlongThreads, smem, s, c.cell_nodes, xc, xf, f.cell_pt_start,
+                  f.pt_node, f.pt_cell, xi_for<T>(f), c.n_cells, nch, G, B);
 }
 
 template <int D, int K, typename T>

@@ -46,6 +46,8 @@ __global__ void __launch_bounds__(128, F == 1 ? NNMG_RESTRICT_MIN_BLOCKS : 4) re
     const T* __restrict__ rf, T* __restrict__ tres, T* __restrict__ buf,
     const int32_t* __restrict__ cell_pt_start, const int32_t* __restrict__ pt_node,
     const T* __restrict__ pt_xi, int64_t n_cells, int nch, Basis1D<T> B) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N = K + 1;
   constexpr int NL = ipow<N, D>::value;
   constexpr int NO = F == 1 ? NL / N : N;         // owned lines (i[, j]) or planes (i)
@@ -192,6 +194,8 @@ template <typename T>
 __global__ void restrict_gather_kernel(const T* __restrict__ buf, const int32_t* __restrict__ gstart,
                                        const int32_t* __restrict__ gpos, T* __restrict__ rc,
                                        int64_t n_nodes, int nch) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_nodes * nch) return;
   const int64_t node = e / nch;
@@ -250,9 +254,8 @@ cudaError_t restrict_run(const DevLevel& f, const DevLevel& c, const T* rf, T* t
     granted = smem;
   }
   const unsigned blocks = (unsigned)((c.n_cells + warps - 1) / warps);
-  kern<<<blocks, 32 * warps, smem, s>>>(rf, tres, buf, f.cell_pt_start, f.pt_node, xi_for<T>(f),
-                                        c.n_cells, nch, B);
-  return cudaGetLastError();
+  return launch_k(kern, blocks, 32 * warps, smem, s, rf, tres, buf, f.cell_pt_start, f.pt_node,
+                  xi_for<T>(f), c.n_cells, nch, B);
 }
 
 template <int D, int K, typename T>
@@ -310,9 +313,8 @@ cudaError_t launch_restrict_gather(const DevLevel& coarse, const T* scratch, T* 
                                    cudaStream_t s) {
   const int64_t n = coarse.n_nodes * nch;
   if (n == 0) return cudaSuccess;
-  restrict_gather_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-      scratch, coarse.gather_start, coarse.gather_pos, rc, coarse.n_nodes, nch);
-  return cudaGetLastError();
+  return launch_k(restrict_gather_kernel<T>, (unsigned)((n + 255) / 256), 256, 0, s, scratch,
+                  coarse.gather_start, coarse.gather_pos, rc, coarse.n_nodes, nch);
 }
 
 template cudaError_t launch_restrict_points<float>(const DevLevel&, const DevLevel&, const float*,

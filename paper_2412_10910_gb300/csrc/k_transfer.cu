@@ -29,6 +29,8 @@ __global__ void __launch_bounds__(32 * kCoarseWarps) coarse_solve_kernel(
     const double* __restrict__ Ainv, const int32_t* __restrict__ rows, int n,
     const TI* __restrict__ r, TO* __restrict__ z, int nrhs, int npad,
     double* __restrict__ partial) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double sr[kCoarseTile * kMaxRhs];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rpw = 32 / npad;                       // rows per warp
@@ -67,6 +69,8 @@ __global__ void __launch_bounds__(32 * kCoarseWarps) coarse_solve_kernel(
 template <typename TO>
 __global__ void coarse_sum_kernel(const double* __restrict__ partial, const int32_t* __restrict__ rows,
                                   int n, int nseg, TO* __restrict__ z, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * nrhs) return;
   const int i = e / nrhs, q = e - i * nrhs;
@@ -323,13 +327,11 @@ cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs,
   int nseg = (int)std::min<int64_t>(kCoarseMaxSegments, std::max<int64_t>(1, (4 * 152) / blocks));
   nseg = std::max(1, std::min(nseg, (n + kCoarseTile - 1) / kCoarseTile));
   if (!L.coarse_partial) nseg = 1;
-  coarse_solve_kernel<TI, TO><<<dim3(blocks, nseg), 32 * kCoarseWarps, 0, s>>>(
-      L.coarse_inv, L.free_rows, n, r, z, nrhs, npad, L.coarse_partial);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(coarse_solve_kernel<TI, TO>, dim3(blocks, nseg), 32 * kCoarseWarps, 0, s,
+                           L.coarse_inv, L.free_rows, n, r, z, nrhs, npad, L.coarse_partial);
   if (e != cudaSuccess || nseg == 1) return e;
-  coarse_sum_kernel<TO><<<(n * nrhs + 255) / 256, 256, 0, s>>>(L.coarse_partial, L.free_rows, n,
-                                                               nseg, z, nrhs);
-  return cudaGetLastError();
+  return launch_k(coarse_sum_kernel<TO>, (n * nrhs + 255) / 256, 256, 0, s, L.coarse_partial,
+                  L.free_rows, n, nseg, z, nrhs);
 }
 
 template cudaError_t launch_prolongate_add<float>(const DevLevel&, const DevLevel&, const float*,

@@ -43,6 +43,8 @@ inline unsigned vblocks(int64_t n) {
 template <typename T>
 __global__ void cheb_init_kernel(const T* __restrict__ f, const T* __restrict__ dinv,
                                  T* __restrict__ d, T* __restrict__ x, T c, int64_t n, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   const unsigned un = (unsigned)n, ur = (unsigned)nrhs;
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < un; e += gridDim.x * blockDim.x) {
     const T v = c * dinv[e / ur] * f[e];
@@ -58,6 +60,8 @@ template <typename T>
 __global__ void cheb_step_kernel(const T* __restrict__ f, T* __restrict__ t,
                                  const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x,
                                  T cd, T cr, int64_t n, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   const unsigned un = (unsigned)n, ur = (unsigned)nrhs;
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < un; e += gridDim.x * blockDim.x) {
     const T fe = f[e], te = t[e], de = d[e], xe = x[e], di = dinv[e / ur];
@@ -71,6 +75,8 @@ __global__ void cheb_step_kernel(const T* __restrict__ f, T* __restrict__ t,
 template <typename T>
 __global__ void residual_kernel(const T* __restrict__ f, T* __restrict__ t, T* __restrict__ r,
                                 int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n;
        e += gridDim.x * blockDim.x) {
     r[e] = f[e] - t[e];
@@ -80,6 +86,8 @@ __global__ void residual_kernel(const T* __restrict__ f, T* __restrict__ t, T* _
 
 template <typename TI, typename TO>
 __global__ void cast_kernel(const TI* __restrict__ a, TO* __restrict__ b, int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n;
        e += gridDim.x * blockDim.x)
     b[e] = (TO)a[e];
@@ -111,6 +119,8 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const double* __restri
                                                           const TB* __restrict__ b,
                                                           double* __restrict__ partial,
                                                           int64_t rows, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   const unsigned act = dot_threads(nrhs);
   const unsigned n = (unsigned)(rows * nrhs);
   double v = 0.0;
@@ -136,6 +146,8 @@ __global__ void __launch_bounds__(kDotThreads) pcg_init_kernel(
     const double* __restrict__ b, const uint8_t* __restrict__ row_free, double* __restrict__ r,
     float* __restrict__ r32, double* __restrict__ x, double* __restrict__ p,
     double* __restrict__ partial, int64_t rows, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   const unsigned act = dot_threads(nrhs);
   const unsigned n = (unsigned)(rows * nrhs);
   double v = 0.0;
@@ -181,6 +193,8 @@ __device__ __forceinline__ void start_column(PcgScalars* sc, int q, double bn, b
 
 __global__ void pcg_start_kernel(PcgScalars* sc, const double* partial, int nrhs, double rtol,
                                  int maxit) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int act[kMaxRhs];
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double bn = q < nrhs ? sqrt(sum_partials_warp(partial, q)) : 0.0;
@@ -240,6 +254,8 @@ __global__ void batch_admit_scalar_kernel(PcgScalars* sc, const double* partial,
 
 // rho_new = r.z; beta = rho_new/rho (0 on the first iteration); rho = rho_new
 __global__ void pcg_beta_kernel(PcgScalars* sc, const double* partial, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q < nrhs) {
     const double rn = sum_partials_warp(partial, q);
@@ -263,6 +279,8 @@ __global__ void __launch_bounds__(kDotThreads) pcg_p_kernel(const PcgScalars* __
                                                             const TZ* __restrict__ z,
                                                             double* __restrict__ p, int64_t n,
                                                             int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   // the dot-product layout: this thread's elements all lie in column t % nrhs
   const unsigned act = dot_threads(nrhs);
   if (threadIdx.x >= act) return;
@@ -285,6 +303,8 @@ __global__ void __launch_bounds__(kDotThreads) pcg_p_kernel(const PcgScalars* __
 
 // alpha = rho / (p.q); breakdown if p.q <= 0 or non-finite on an active column
 __global__ void pcg_alpha_kernel(PcgScalars* sc, const double* partial, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= nrhs) return;
   const double pq = sum_partials_warp(partial, q);
@@ -311,6 +331,8 @@ __global__ void __launch_bounds__(kDotThreads) pcg_update_kernel(
     const PcgScalars* __restrict__ sc, const double* __restrict__ p, double* __restrict__ qv,
     double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32,
     double* __restrict__ partial, int64_t rows, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   const unsigned act = dot_threads(nrhs);
   const unsigned n = (unsigned)(rows * nrhs);
   double v = 0.0;
@@ -346,6 +368,8 @@ __global__ void pcg_loop_next_kernel(cudaGraphConditionalHandle hc, const PcgSca
 }
 
 __global__ void pcg_check_kernel(PcgScalars* sc, const double* partial, int nrhs) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int act[kMaxRhs];
   __shared__ int bad[kMaxRhs];
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -429,8 +453,7 @@ cudaError_t launch_cheb_init(const T* f, const T* dinv, T* d, T* x, double c, in
   const int64_t n = rows * nrhs;
   if (n == 0) return cudaSuccess;
   if (too_big(n)) return cudaErrorInvalidValue;
-  cheb_init_kernel<T><<<vblocks(n), 256, 0, s>>>(f, dinv, d, x, (T)c, n, nrhs);
-  return cudaGetLastError();
+  return launch_k(cheb_init_kernel<T>, vblocks(n), 256, 0, s, f, dinv, d, x, (T)c, n, nrhs);
 }
 template <typename T>
 cudaError_t launch_cheb_step(const T* f, T* t, const T* dinv, T* d, T* x, double cd, double cr,
@@ -438,43 +461,37 @@ cudaError_t launch_cheb_step(const T* f, T* t, const T* dinv, T* d, T* x, double
   const int64_t n = rows * nrhs;
   if (n == 0) return cudaSuccess;
   if (too_big(n)) return cudaErrorInvalidValue;
-  cheb_step_kernel<T><<<vblocks(n), 256, 0, s>>>(f, t, dinv, d, x, (T)cd, (T)cr, n, nrhs);
-  return cudaGetLastError();
+  return launch_k(cheb_step_kernel<T>, vblocks(n), 256, 0, s, f, t, dinv, d, x, (T)cd, (T)cr, n, nrhs);
 }
 template <typename T>
 cudaError_t launch_residual(const T* f, T* t, T* r, int64_t rows, int nrhs, cudaStream_t s) {
   const int64_t n = rows * nrhs;
   if (n == 0) return cudaSuccess;
   if (too_big(n)) return cudaErrorInvalidValue;
-  residual_kernel<T><<<vblocks(n), 256, 0, s>>>(f, t, r, n);
-  return cudaGetLastError();
+  return launch_k(residual_kernel<T>, vblocks(n), 256, 0, s, f, t, r, n);
 }
 template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* a, TO* b, int64_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   if (too_big(n)) return cudaErrorInvalidValue;
-  cast_kernel<TI, TO><<<vblocks(n), 256, 0, s>>>(a, b, n);
-  return cudaGetLastError();
+  return launch_k(cast_kernel<TI, TO>, vblocks(n), 256, 0, s, a, b, n);
 }
 template <typename TB>
 cudaError_t launch_dot_partial(const double* a, const TB* b, double* partial, int64_t rows,
                                int nrhs, cudaStream_t s) {
   if (too_big(rows * nrhs)) return cudaErrorInvalidValue;
-  dot_kernel<TB><<<kDotBlocks, kDotThreads, 0, s>>>(a, b, partial, rows, nrhs);
-  return cudaGetLastError();
+  return launch_k(dot_kernel<TB>, kDotBlocks, kDotThreads, 0, s, a, b, partial, rows, nrhs);
 }
 cudaError_t launch_pcg_init(const double* b, const uint8_t* row_free, double* r, float* r32,
                             double* x, double* p, double* partial, int64_t rows, int nrhs,
                             cudaStream_t s) {
   if (too_big(rows * nrhs)) return cudaErrorInvalidValue;
-  pcg_init_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, row_free, r, r32, x, p, partial, rows,
-                                                     nrhs);
-  return cudaGetLastError();
+  return launch_k(pcg_init_kernel, kDotBlocks, kDotThreads, 0, s, b, row_free, r, r32, x, p, partial,
+                  rows, nrhs);
 }
 cudaError_t launch_pcg_start(PcgScalars* sc, const double* partial, int nrhs, double rtol,
                              int maxit, cudaStream_t s) {
-  pcg_start_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs, rtol, maxit);
-  return cudaGetLastError();
+  return launch_k(pcg_start_kernel, 1, 32 * kMaxRhs, 0, s, sc, partial, nrhs, rtol, maxit);
 }
 cudaError_t launch_batch_reset(PcgScalars* sc, double rtol, int maxit, cudaStream_t s) {
   batch_reset_kernel<<<1, 32, 0, s>>>(sc, rtol, maxit);
@@ -493,24 +510,22 @@ cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double*
 template <typename TZ>
 cudaError_t launch_pcg_beta_p(PcgScalars* sc, const double* partial, const TZ* z, double* p,
                               int64_t rows, int nrhs, cudaStream_t s) {
-  pcg_beta_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs);
+  cudaError_t eb = launch_k(pcg_beta_kernel, 1, 32 * kMaxRhs, 0, s, sc, partial, nrhs);
+  if (eb != cudaSuccess) return eb;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = rows * nrhs;
   if (too_big(n)) return cudaErrorInvalidValue;
-  pcg_p_kernel<TZ><<<kDotBlocks, kDotThreads, 0, s>>>(sc, z, p, n, nrhs);
-  return cudaGetLastError();
+  return launch_k(pcg_p_kernel<TZ>, kDotBlocks, kDotThreads, 0, s, sc, z, p, n, nrhs);
 }
 cudaError_t launch_pcg_alpha(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s) {
-  pcg_alpha_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs);
-  return cudaGetLastError();
+  return launch_k(pcg_alpha_kernel, 1, 32 * kMaxRhs, 0, s, sc, partial, nrhs);
 }
 cudaError_t launch_pcg_update(const PcgScalars* sc, const double* p, double* q, double* x,
                               double* r, float* r32, double* partial, int64_t rows, int nrhs,
                               cudaStream_t s) {
   if (too_big(rows * nrhs)) return cudaErrorInvalidValue;
-  pcg_update_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(sc, p, q, x, r, r32, partial, rows, nrhs);
-  return cudaGetLastError();
+  return launch_k(pcg_update_kernel, kDotBlocks, kDotThreads, 0, s, sc, p, q, x, r, r32, partial, rows, nrhs);
 }
 cudaError_t launch_pcg_loop_begin(cudaGraphConditionalHandle hc, const PcgScalars* sc, int* count,
                                   cudaStream_t s) {
@@ -523,8 +538,7 @@ cudaError_t launch_pcg_loop_next(cudaGraphConditionalHandle hc, const PcgScalars
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s) {
-  pcg_check_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, nrhs);
-  return cudaGetLastError();
+  return launch_k(pcg_check_kernel, 1, 32 * kMaxRhs, 0, s, sc, partial, nrhs);
 }
 cudaError_t launch_axpby_dinv(const double* u, const double* dinv, const double* vprev,
                               double beta, double* w, int64_t rows, cudaStream_t s) {

@@ -18,6 +18,13 @@
 using namespace nnmg;
 
 namespace nnmg {
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("NNMG_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 cudaError_t launch_finalize_diag(const double* diag, const uint8_t* row_free, double* dinv64,
                                  float* dinv32, int64_t rows, cudaStream_t s);
 }
