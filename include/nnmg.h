@@ -263,7 +263,12 @@ int nnmg_set_nested(nnmg_handle* h, int fine_level, const int32_t* parent_cell,
 
 /* One V-cycle (Algorithm 1) on the finest level from a zero guess: z ~ A_L^-1 r.
  * Chebyshev-Jacobi pre- and post-smoothing, residual, restriction, recursion,
- * prolongation; coarsest level solved directly in FP64. */
+ * prolongation; coarsest level solved directly in FP64.  With the environment
+ * variable NNMG_FUSED_SMOOTHER=1 each smoothing sweep of a small level served
+ * by the register operator runs as one persistent cooperative kernel (grid
+ * barriers between its operator and vector phases; not used by handles in
+ * continuous batching); by default every step is its own kernel, which
+ * measured faster inside the captured graph. */
 int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
                 void* stream);
 

@@ -532,21 +532,17 @@ __device__ __forceinline__ void sweep(const T (&M)[kMaxN][kMaxN], const T* f, T*
   }
 }
 
+// y += A_K x on one (cell, right-hand side) unit (the body of the register
+// kernel and of the persistent smoother's operator phase).
 template <int D, int K, typename T>
-__global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__ cell_nodes,
-                                                     const T* __restrict__ metric,
-                                                     const typename io_of<T>::type* __restrict__ x,
-                                                     typename io_of<T>::type* __restrict__ y,
-                                                     int64_t n_cells, int nrhs, Basis1D<T> B) {
-  pdl_trigger();
-  pdl_wait();
+__device__ __forceinline__ void op_reg_unit(const int32_t* __restrict__ cell_nodes,
+                                            const T* __restrict__ metric,
+                                            const typename io_of<T>::type* __restrict__ x,
+                                            typename io_of<T>::type* __restrict__ y, int64_t cell,
+                                            int rhs, int nrhs, const Basis1D<T>& B) {
   constexpr int N = K + 1;
   constexpr int NQ = D == 2 ? N * N : N * N * N;
   constexpr int NM = D == 2 ? 3 : 6;
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t cell = u / nrhs;
-  if (cell >= n_cells) return;
-  const int rhs = (int)(u - cell * nrhs);
   const int32_t* cn = cell_nodes + cell * NQ;
   T v[NQ], gx[NQ], gy[NQ];
 #pragma unroll
@@ -593,6 +589,138 @@ __global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__
   for (int i = 0; i < NQ; ++i) {
     const int dof = cn[i];
     if (dof >= 0) add_out(&y[(int64_t)dof * nrhs + rhs], v[i]);
+  }
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__ cell_nodes,
+                                                     const T* __restrict__ metric,
+                                                     const typename io_of<T>::type* __restrict__ x,
+                                                     typename io_of<T>::type* __restrict__ y,
+                                                     int64_t n_cells, int nrhs, Basis1D<T> B) {
+  pdl_trigger();
+  pdl_wait();
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cell = u / nrhs;
+  if (cell >= n_cells) return;
+  op_reg_unit<D, K, T>(cell_nodes, metric, x, y, cell, (int)(u - cell * nrhs), nrhs, B);
+}
+
+// ------------------------------------------------------ persistent smoother
+// One Chebyshev-Jacobi smoothing sweep (Sec. 4) in a single cooperative
+// launch: the operator phase t = A x (the register kernel's cell body over a
+// grid-stride range of units) and the vector phase d = cd d + cr D^-1 (f - t),
+// x += d, t = 0 alternate, separated by grid-wide barriers.  Pre-smoothing
+// starts from x = d = D^-1 f / theta and ends with t = A x (the residual's
+// operator pass, read by the restriction); post-smoothing starts with an
+// operator pass.  A barrier gives up after kBarrierSpins polls, sets *err and
+// the kernel returns (with a cooperative launch every block is resident, so
+// the limit is a guard, not a schedule).
+constexpr unsigned kBarrierSpins = 1u << 26;   // with a 64 ns pause: a few seconds
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);                       // the next barrier counts from zero
+      __threadfence();
+      atomicAdd(bar + 1, 1u);                    // release the other blocks
+    } else {
+      unsigned it = 0;
+      while (*gen == g) {
+        if (++it > kBarrierSpins) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        if (it > 4096) __nanosleep(64);        // poll at full rate first
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+constexpr int kSmootherThreads = 128;
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(kSmootherThreads) cheb_smoother_kernel(
+    const int32_t* __restrict__ cell_nodes, const T* __restrict__ metric, const T* __restrict__ f,
+    T* __restrict__ t, const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x,
+    int64_t n_cells, int64_t rows, int nrhs, Basis1D<T> B, SmootherPlan P, unsigned* bar, int* err) {
+  const int64_t units = n_cells * nrhs, n = rows * nrhs;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int kU = 4;                          // vector elements in flight per thread
+  int j = 0;
+  if (P.from_zero) {
+    const T c = (T)P.c_init;
+    for (int64_t e0 = t0; e0 < n; e0 += kU * stride) {
+      T fe[kU], di[kU];
+#pragma unroll
+      for (int b = 0; b < kU; ++b) {
+        const int64_t e = e0 + b * stride;
+        fe[b] = e < n ? f[e] : T(0);
+        di[b] = e < n ? dinv[e / nrhs] : T(0);
+      }
+#pragma unroll
+      for (int b = 0; b < kU; ++b) {
+        const int64_t e = e0 + b * stride;
+        if (e < n) {
+          const T v = c * di[b] * fe[b];
+          d[e] = v;
+          x[e] = v;
+        }
+      }
+    }
+    j = 1;
+    if (!grid_barrier(bar, err)) return;
+  }
+  for (; j < P.steps; ++j) {
+    for (int64_t u = t0; u < units; u += stride) {
+      const int64_t cell = u / nrhs;
+      op_reg_unit<D, K, T>(cell_nodes, metric, x, t, cell, (int)(u - cell * nrhs), nrhs, B);
+    }
+    if (!grid_barrier(bar, err)) return;
+    const T cd = (T)P.cd[j], cr = (T)P.cr[j];
+    for (int64_t e0 = t0; e0 < n; e0 += kU * stride) {
+      T fe[kU], te[kU], de[kU], xe[kU], di[kU];
+#pragma unroll
+      for (int b = 0; b < kU; ++b) {
+        const int64_t e = e0 + b * stride;
+        const bool in = e < n;
+        fe[b] = in ? f[e] : T(0);
+        te[b] = in ? t[e] : T(0);
+        de[b] = in ? d[e] : T(0);
+        xe[b] = in ? x[e] : T(0);
+        di[b] = in ? dinv[e / nrhs] : T(0);
+      }
+#pragma unroll
+      for (int b = 0; b < kU; ++b) {
+        const int64_t e = e0 + b * stride;
+        if (e < n) {
+          const T dn = cd * de[b] + cr * di[b] * (fe[b] - te[b]);
+          d[e] = dn;
+          x[e] = xe[b] + dn;
+          t[e] = T(0);
+        }
+      }
+    }
+    if (j + 1 < P.steps || P.final_op) {
+      if (!grid_barrier(bar, err)) return;
+    }
+  }
+  if (P.final_op) {
+    for (int64_t u = t0; u < units; u += stride) {
+      const int64_t cell = u / nrhs;
+      op_reg_unit<D, K, T>(cell_nodes, metric, x, t, cell, (int)(u - cell * nrhs), nrhs, B);
+    }
   }
 }
 
@@ -842,6 +970,37 @@ cudaError_t run_reg2(const DevLevel& L, const float* metric, const float* x, flo
                   npair, B);
 }
 
+template <int D, int K, typename T>
+cudaError_t run_smoother(const DevLevel& L, const T* f, T* t, const T* dinv, T* d, T* x, int nrhs,
+                         const SmootherPlan& P, unsigned* bar, int* err, cudaStream_t s) {
+  Basis1D<T> B;
+  pick_basis<T>(K, &B);
+  auto kern = cheb_smoother_kernel<D, K, T>;
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmootherThreads, 0);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t units = L.n_cells * nrhs;
+  const int64_t want = std::max<int64_t>(1, (units + kSmootherThreads - 1) / kSmootherThreads);
+  const unsigned blocks = (unsigned)std::min<int64_t>(want, (int64_t)per_sm * sms);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = blocks;
+  cfg.blockDim = kSmootherThreads;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, (const int32_t*)L.cell_nodes, (const T*)metric_of<T>(L), f,
+                            t, dinv, d, x, L.n_cells, L.rows, nrhs, B, P, bar, err);
+}
+
 // The register-resident kernel serves Poisson cells with at most 27 (3D) or
 // 25 (2D) nodes, in every arithmetic type; units < 0 asks for it explicitly,
 // units = -2 for its paired FP32 form (even
@@ -967,6 +1126,45 @@ int operator_unit_candidates(const DevLevel& L, int nrhs, int* out, int max_out)
   return n;
 }
 
+// The persistent smoother is meant for levels where launches dominate: those
+// whose operator fills at most kSmootherWaves waves of the GPU (4 blocks of
+// 128 threads per SM at the register operator's 128 registers).  On larger
+// levels its vector phase, at the operator's occupancy, loses to the separate
+// vector kernels (config 2's 55^3 fine level: 1.321 vs 1.103 ms per level and
+// V-cycle, eager).
+constexpr int64_t kSmootherWaves = 4;
+bool cheb_smoother_supported(const DevLevel& L, int m, int nrhs) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return false;
+  }
+  const int64_t wave = (int64_t)sms * 4 * 128;
+  return L.n_cells > 0 && reg_eligible<float>(L) && m >= 1 && m <= kMaxChebSteps &&
+         L.n_cells * nrhs <= kSmootherWaves * wave;
+}
+
+template <typename T>
+cudaError_t launch_cheb_smoother(const DevLevel& L, const T* f, T* t, const T* dinv, T* d, T* x,
+                                 int nrhs, const SmootherPlan& P, unsigned* bar, int* err,
+                                 cudaStream_t s) {
+  if (!cheb_smoother_supported(L, P.steps, nrhs)) return cudaErrorNotSupported;
+#define NNMG_S(D, K) \
+  if (L.dim == D && L.k == K) return run_smoother<D, K, T>(L, f, t, dinv, d, x, nrhs, P, bar, err, s);
+  NNMG_S(2, 1) NNMG_S(2, 2) NNMG_S(2, 3) NNMG_S(2, 4) NNMG_S(3, 1) NNMG_S(3, 2)
+#undef NNMG_S
+  return cudaErrorNotSupported;
+}
+
+template cudaError_t launch_cheb_smoother<float>(const DevLevel&, const float*, float*, const float*,
+                                                 float*, float*, int, const SmootherPlan&,
+                                                 unsigned*, int*, cudaStream_t);
+template cudaError_t launch_cheb_smoother<double>(const DevLevel&, const double*, double*,
+                                                  const double*, double*, double*, int,
+                                                  const SmootherPlan&, unsigned*, int*,
+                                                  cudaStream_t);
 template cudaError_t launch_operator<float>(const DevLevel&, const float*, float*, int, double,
                                             double, cudaStream_t, int);
 template cudaError_t launch_operator<double>(const DevLevel&, const double*, double*, int, double,

@@ -367,9 +367,11 @@ __global__ void pcg_loop_next_kernel(cudaGraphConditionalHandle hc, const PcgSca
   cudaGraphSetConditional(hc, (sc->any_active && c < sc->maxit) ? 1u : 0u);
 }
 
-__global__ void pcg_check_kernel(PcgScalars* sc, const double* partial, int nrhs) {
+__global__ void pcg_check_kernel(PcgScalars* sc, const double* partial, int nrhs,
+                                 const int* __restrict__ smoother_err) {
   pdl_trigger();
   pdl_wait();
+  const bool serr = smoother_err && *smoother_err;     // a smoother's grid barrier gave up
   __shared__ int act[kMaxRhs];
   __shared__ int bad[kMaxRhs];
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -377,7 +379,7 @@ __global__ void pcg_check_kernel(PcgScalars* sc, const double* partial, int nrhs
   if (lane == 0) {
     int a = 0, b = 0;
     if (q < nrhs && sc->active[q]) {
-      if (sc->broken[q] || !isfinite(rn)) {
+      if (sc->broken[q] || serr || !isfinite(rn)) {
         sc->broken[q] = 1;
         b = 1;
       } else {
@@ -537,8 +539,9 @@ cudaError_t launch_pcg_loop_next(cudaGraphConditionalHandle hc, const PcgScalars
   pcg_loop_next_kernel<<<1, 1, 0, s>>>(hc, sc, count);
   return cudaGetLastError();
 }
-cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s) {
-  return launch_k(pcg_check_kernel, 1, 32 * kMaxRhs, 0, s, sc, partial, nrhs);
+cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, const int* smoother_err,
+                             cudaStream_t s) {
+  return launch_k(pcg_check_kernel, 1, 32 * kMaxRhs, 0, s, sc, partial, nrhs, smoother_err);
 }
 cudaError_t launch_axpby_dinv(const double* u, const double* dinv, const double* vprev,
                               double beta, double* w, int64_t rows, cudaStream_t s) {

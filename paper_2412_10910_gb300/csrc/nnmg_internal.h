@@ -232,6 +232,28 @@ cudaError_t launch_restrict_gather(const DevLevel& coarse, const T* scratch, T* 
 template <typename TI, typename TO>
 cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs, cudaStream_t s);
 
+// One Chebyshev-Jacobi smoothing sweep as a single persistent (cooperative)
+// kernel for small levels served by the register operator (Poisson, 3D k <= 2,
+// 2D; at most a few waves of operator work, see cheb_smoother_supported):
+// steps m; from_zero: start x = d = c_init D^-1 f (pre-smoothing) instead of
+// an operator pass; step j (j >= 1 from zero, j >= 0 otherwise) computes
+// t = A x, then d = cd[j] d + cr[j] D^-1 (f - t), x += d, t = 0; final_op
+// ends with t = A x.  bar: two zeroed device words (barrier count and
+// generation) owned by the caller; err: set to 1 if a grid barrier gave up.
+// Returns cudaErrorNotSupported when the level has no fused form.
+constexpr int kMaxChebSteps = 16;
+struct SmootherPlan {
+  int steps = 0, from_zero = 0, final_op = 0;
+  double c_init = 0.0;
+  double cd[kMaxChebSteps] = {0}, cr[kMaxChebSteps] = {0};
+};
+// Whether launch_cheb_smoother serves this level with m steps and nrhs columns.
+bool cheb_smoother_supported(const DevLevel& L, int m, int nrhs);
+template <typename T>
+cudaError_t launch_cheb_smoother(const DevLevel& L, const T* f, T* t, const T* dinv, T* d, T* x,
+                                 int nrhs, const SmootherPlan& P, unsigned* bar, int* err,
+                                 cudaStream_t s);
+
 // vector kernels, rows x nrhs
 template <typename T>
 cudaError_t launch_cheb_init(const T* f, const T* dinv, T* d, T* x, double c, int64_t rows,
@@ -287,7 +309,9 @@ cudaError_t launch_pcg_alpha(PcgScalars* sc, const double* partial, int nrhs, cu
 cudaError_t launch_pcg_update(const PcgScalars* sc, const double* p, double* q, double* x,
                               double* r, float* r32, double* partial, int64_t rows, int nrhs,
                               cudaStream_t s);
-cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, cudaStream_t s);
+// smoother_err (may be null): a set flag marks every active column broken.
+cudaError_t launch_pcg_check(PcgScalars* sc, const double* partial, int nrhs, const int* smoother_err,
+                             cudaStream_t s);
 // Loop control of the device-side PCG loop (graph conditional WHILE node).
 cudaError_t launch_pcg_loop_begin(cudaGraphConditionalHandle hc, const PcgScalars* sc, int* count,
                                   cudaStream_t s);

@@ -38,6 +38,11 @@ struct WorkSet {
 struct nnmg_handle {
   nnmg_options opt;
   int device = -1;                  // the device current at setup
+  // persistent smoother: grid barrier count and generation, then its error flag
+  unsigned* smoother_sync = nullptr;
+  // cooperative (persistent) smoother kernels allowed; off once the handle
+  // serves continuous batching, whose engines run concurrently on other streams
+  bool cooperative_ok = true;
   void* noalloc_scratch = nullptr;  // device address of nnmg_restrict_noalloc's array there
   std::vector<DevLevel> lv;
   cudaStream_t cap = nullptr;
@@ -115,6 +120,10 @@ int ensure_work(nnmg_handle* h) {
   if (W.ready) return NNMG_OK;
   const int n = (int)h->lv.size();
   const int mr = h->opt.max_nrhs;
+  if (!h->smoother_sync) {
+    CK(dalloc(h, &h->smoother_sync, 4, true));
+    CK(cudaMemset(h->smoother_sync, 0, 4 * sizeof(unsigned)));
+  }
   W.f.assign(n, nullptr);
   W.x.assign(n, nullptr);
   W.t.assign(n, nullptr);
@@ -282,6 +291,59 @@ struct VcycleTimer {
   cudaError_t stop(cudaStream_t s) { return cudaEventRecord(marks.back().b, s); }
 };
 
+// Forget the captured V-cycle, iteration and loop graphs (they are captured
+// again on later calls).  The caller makes sure none is running.
+void drop_graphs(nnmg_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  h->runs.clear();
+  for (auto& kv : h->loops)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  h->loops.clear();
+}
+
+int* smoother_err(nnmg_handle* h) {
+  return h->smoother_sync ? reinterpret_cast<int*>(h->smoother_sync + 2) : nullptr;
+}
+
+// The persistent smoother (one cooperative kernel per Chebyshev sweep) serves
+// small levels whose operator is the register kernel (autotuned choice -1, or
+// the default rule) when NNMG_FUSED_SMOOTHER=1 is set.  It is off by default:
+// inside the captured V-cycle graph a kernel boundary costs about a
+// microsecond and the grid barriers more, so the kernel-per-step sequence is
+// faster (config 2 V-cycle 1.327 ms without, 1.358 ms with the smoother on its
+// three coarser levels, 1.622 ms with it on every level; config 1 solve 0.83 ms
+// either way).
+bool fused_smoother_allowed(const nnmg_handle* h, const DevLevel& L, int op_choice, int m,
+                            int nrhs) {
+  const char* e = getenv("NNMG_FUSED_SMOOTHER");    // read when a V-cycle is enqueued or captured
+  const bool on = e && e[0] == '1';
+  return on && h->cooperative_ok && (op_choice == -1 || op_choice == 0) &&
+         cheb_smoother_supported(L, m, nrhs);
+}
+
+// Chebyshev coefficients of one sweep (Sec. 4 smoother; the recurrence of
+// the kernel-per-step path): pre-smoothing from zero, or continuing from x.
+SmootherPlan smoother_plan(const DevLevel& L, int m, bool pre) {
+  SmootherPlan P;
+  const double a = L.cheb_a, b = L.cheb_b;
+  const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
+  P.steps = m;
+  P.from_zero = pre ? 1 : 0;
+  P.final_op = pre ? 1 : 0;
+  P.c_init = 1.0 / theta;
+  P.cd[0] = 0.0;
+  P.cr[0] = 1.0 / theta;
+  double rho = 1.0 / sigma;
+  for (int j = 1; j < m && j < kMaxChebSteps; ++j) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    P.cd[j] = rn * rho;
+    P.cr[j] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  return P;
+}
+
 template <typename T>
 cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_t s,
                            VcycleTimer* P = nullptr) {
@@ -310,19 +372,30 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
     const int ou = op_units<T>(h, l, nrhs, s);
     const double a = L.cheb_a, b = L.cheb_b;
     const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
-    RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
-        launch_cheb_init<T>(f, dinv, d, x, 1.0 / theta, L.rows, nrhs, s));
-    double rho = 1.0 / sigma;
-    for (int j = 1; j < m; ++j) {
+    // pre-smoothing and the residual's operator pass in one persistent kernel
+    // where the level has one, else kernel by kernel
+    bool fused = false;
+    if (fused_smoother_allowed(h, L, ou, m, nrhs)) {
       RUN(l, NNMG_PROF_PRE, NNMG_PROF_OPERATOR,
-          launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
-      const double rn = 1.0 / (2.0 * sigma - rho);
-      RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
-          launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
-      rho = rn;
+          launch_cheb_smoother<T>(L, f, t, dinv, d, x, nrhs, smoother_plan(L, m, true),
+                                  h->smoother_sync, smoother_err(h), s));
+      fused = true;
     }
-    RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_OPERATOR,
-        launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+    if (!fused) {
+      RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
+          launch_cheb_init<T>(f, dinv, d, x, 1.0 / theta, L.rows, nrhs, s));
+      double rho = 1.0 / sigma;
+      for (int j = 1; j < m; ++j) {
+        RUN(l, NNMG_PROF_PRE, NNMG_PROF_OPERATOR,
+            launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
+            launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
+        rho = rn;
+      }
+      RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_OPERATOR,
+          launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+    }
     // r_l = f_l - A_l x_l formed inside the restriction (t reset to zero there)
     RUN(l, NNMG_PROF_RESTRICT, NNMG_PROF_RESTRICT,
         launch_restrict_residual<T>(L, h->lv[l - 1], f, t, d, W.f[l - 1], W.scratch[l], nrhs, s));
@@ -342,6 +415,12 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
     const int ou = op_units<T>(h, l, nrhs, s);
     const double a = L.cheb_a, b = L.cheb_b;
     const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
+    if (fused_smoother_allowed(h, L, ou, m, nrhs)) {
+      RUN(l, NNMG_PROF_POST, NNMG_PROF_OPERATOR,
+          launch_cheb_smoother<T>(L, f, t, dinv, d, x, nrhs, smoother_plan(L, m, false),
+                                  h->smoother_sync, smoother_err(h), s));
+      continue;
+    }
     double rho = 1.0 / sigma;
     RUN(l, NNMG_PROF_POST, NNMG_PROF_OPERATOR, launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
     RUN(l, NNMG_PROF_POST, NNMG_PROF_VECTOR,
@@ -390,7 +469,7 @@ cudaError_t enqueue_pcg_iter(nnmg_handle* h, int mode, int nrhs, cudaStream_t s)
   if ((e = launch_dot_partial<double>(h->pp, h->pq, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
   if ((e = launch_pcg_alpha(h->sc, h->partial, nrhs, s)) != cudaSuccess) return e;
   if ((e = launch_pcg_update(h->sc, h->pp, h->pq, h->px, h->pr, h->pr32, h->partial, rows, nrhs, s)) != cudaSuccess) return e;
-  return launch_pcg_check(h->sc, h->partial, nrhs, s);
+  return launch_pcg_check(h->sc, h->partial, nrhs, smoother_err(h), s);
 }
 
 // Run `body` on stream s: eagerly on the first call for `key`, from a captured
@@ -1371,12 +1450,7 @@ int nnmg_set_nested(nnmg_handle* h, int fine_level, const int32_t* parent_cell,
   }
   DevLevel& F = h->lv[fine_level];
   const DevLevel& C = h->lv[fine_level - 1];
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);   // the V-cycle changes
-  h->graphs.clear();
-  h->runs.clear();
-  for (auto& kv : h->loops)
-    if (kv.second) cudaGraphExecDestroy(kv.second);
-  h->loops.clear();
+  drop_graphs(h);                                                  // the V-cycle changes
   if (!parent_cell) {
     F.gc_active = false;
     return NNMG_OK;
@@ -1416,6 +1490,13 @@ int nnmg_batch_reset(nnmg_handle* h, int mode, int nslots, double rtol, int maxi
     return NNMG_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (h->cooperative_ok) {
+    // from now on kernel-per-step smoothing: drop graphs captured with the
+    // cooperative smoother
+    h->cooperative_ok = false;
+    NNMG_CUDA(cudaStreamSynchronize(s));
+    drop_graphs(h);
+  }
   if ((rc = ensure_pcg(h))) return rc;
   if ((rc = (mode == NNMG_FP64_MG ? ensure_work<double>(h) : ensure_work<float>(h)))) return rc;
   if (mode == NNMG_FP32_MG_DW_CG && (rc = ensure_dw(h, (int)h->lv.size() - 1))) return rc;

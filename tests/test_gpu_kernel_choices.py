@@ -151,3 +151,42 @@ def test_operator_choice_and_setup_phases_are_reported(monkeypatch):
                 H.operator_choice(*bad)
     finally:
         H.close()
+
+
+@pytest.mark.parametrize("name", ["c1_q1", "c1_q2_16rhs", "c2_q2_3lev", "c3_q4_pmg"])
+def test_vcycle_and_pcg_with_and_without_persistent_smoother(name, monkeypatch):
+    """The persistent smoother (one cooperative kernel per Chebyshev sweep on
+    levels served by the register operator) and the kernel-per-step sequence
+    give the same V-cycle and PCG: both against the oracle at the parity
+    tolerances, and the same iteration counts."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_10910_gb300 import _abi
+    levels, O = oracle_case(name)
+    nrhs = CASES[name][5]
+    top = len(O.levels) - 1
+    r = rng_vec(O.levels[top].n, nrhs, 41)
+    r[np.repeat(O.levels[top].constrained, O.ncomp)] = 0.0
+    zo = O.vcycle(r, "fp64")
+    r32 = torch.tensor(r, dtype=torch.float32, device="cuda")
+    zo32 = O.vcycle(r32.double().cpu().numpy(), "fp32")
+    its = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("NNMG_FUSED_SMOOTHER", fused)
+        H = gpu_case(name, levels)
+        try:
+            for rep in range(2):               # eager, then the captured graph
+                z = H.vector(top, nrhs)
+                H.vcycle(torch.tensor(r, device="cuda"), z)
+                assert _relmax(z.cpu().numpy(), zo) <= 1e-9, (fused, rep)
+                z32 = H.vector(top, nrhs, torch.float32)
+                H.vcycle(r32, z32)
+                assert _relmax(z32.double().cpu().numpy(), zo32) <= 2e-5, (fused, rep)
+            b = torch.tensor(r, device="cuda")
+            x = H.vector(top, nrhs)
+            st, it, rel = H.pcg(b, x, mode=_abi.FP32_MG_FP64_CG, rtol=1e-8, maxit=100)
+            assert st == 0 and np.all(rel <= 1e-8)
+            its[fused] = list(it)
+        finally:
+            H.close()
+    assert its["1"] == its["0"]
