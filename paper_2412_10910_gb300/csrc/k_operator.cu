@@ -80,6 +80,37 @@ struct metric_type<f2> {
 __device__ __forceinline__ f2 to_arith(float2 v, f2) { return f2(v); }
 __device__ __forceinline__ void add_out(float2* p, f2 v) { atomicAdd(p, v.v); }
 
+// Metric rows are padded to NQP = NQ rounded up to a multiple of 4 entries, so
+// every row of every cell starts on a 16-byte boundary; the register kernels
+// load a row four (FP32) or two (FP64, double-word) quadrature points at a time.
+__host__ __device__ constexpr int padded_nq(int nq) { return (nq + 3) / 4 * 4; }
+template <typename T>
+struct MetricVec {
+  static constexpr int W = 16 / (int)sizeof(T);
+};
+__device__ __forceinline__ void load_metric(const float* p, float (&o)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = a.z;
+  o[3] = a.w;
+}
+__device__ __forceinline__ void load_metric(const float* p, float (&o)[2]) {
+  const float2 a = *reinterpret_cast<const float2*>(p);
+  o[0] = a.x;
+  o[1] = a.y;
+}
+__device__ __forceinline__ void load_metric(const double* p, double (&o)[2]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  o[0] = a.x;
+  o[1] = a.y;
+}
+__device__ __forceinline__ void load_metric(const dw* p, dw (&o)[2]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  o[0] = dw(a.x, a.y);
+  o[1] = dw(a.z, a.w);
+}
+
 // The two 1D matrices of the sweeps: S interpolates from the Lobatto nodes to
 // the Gauss points, Dg differentiates by collocation on the Gauss points.  For
 // odd N the middle Gauss point is the middle Lobatto node (both are 1/2), so
@@ -178,7 +209,7 @@ __device__ __forceinline__ void op3d_body(const int32_t* __restrict__ cell_nodes
                                           int nrhs, int U, const Basis1D<T>& B, T lambda, T mu) {
   pdl_trigger();
   pdl_wait();
-  constexpr int N = K + 1, N2 = N * N, NQ = N2 * N;
+  constexpr int N = K + 1, N2 = N * N, NQ = N2 * N, NQP = padded_nq(NQ);
   constexpr int NM = NC == 1 ? 6 : 9;
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -196,7 +227,7 @@ __device__ __forceinline__ void op3d_body(const int32_t* __restrict__ cell_nodes
   // P0 + P1: gather the z-line (i=a, j=b) and interpolate along z in registers
 #pragma unroll
   for (int l = 0; l < N; ++l) dof[l] = act ? cell_nodes[cell * NQ + a + N * b + N2 * l] : -1;
-  const typename metric_type<T>::type* mc = metric + (act ? cell : 0) * NM * NQ;
+  const typename metric_type<T>::type* mc = metric + (act ? cell : 0) * NM * NQP;
   // Poisson: fetch the metric terms of this thread's quadrature column now, so
   // that their latency overlaps the first sweeps (used in P5)
   T Gp[NC == 1 ? 6 : 1][N];
@@ -204,7 +235,7 @@ __device__ __forceinline__ void op3d_body(const int32_t* __restrict__ cell_nodes
 #pragma unroll
     for (int q = 0; q < N; ++q)
 #pragma unroll
-      for (int m = 0; m < 6; ++m) Gp[m][q] = act ? T(mc[m * NQ + a + N * b + N2 * q]) : T(0);
+      for (int m = 0; m < 6; ++m) Gp[m][q] = act ? T(mc[m * NQP + a + N * b + N2 * q]) : T(0);
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -291,7 +322,7 @@ __device__ __forceinline__ void op3d_body(const int32_t* __restrict__ cell_nodes
           g[c][2] = gz[c][q];
         }
 #pragma unroll
-        for (int m = 0; m < 9; ++m) Km[m / 3][m % 3] = act ? T(mc[m * NQ + idx]) : T(0);
+        for (int m = 0; m < 9; ++m) Km[m / 3][m % 3] = act ? T(mc[m * NQP + idx]) : T(0);
         elastic_flux(g, Km, lambda, mu, F);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -459,13 +490,14 @@ __global__ void op2d_kernel(const int32_t* __restrict__ cell_nodes, const T* __r
 #pragma unroll
     for (int p = 0; p < N; ++p) u[p] = S(0, a + N * p);
     apply<N, kDeriv>(B.Dg, u, gy);
-    const T* mc = metric + (act ? cell : 0) * 3 * NQ;
+    constexpr int NQP = padded_nq(NQ);
+    const T* mc = metric + (act ? cell : 0) * 3 * NQP;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       const int idx = a + N * q;
       const T gx = S(1, idx);
-      const T G0 = act ? mc[idx] : T(0), G1 = act ? mc[NQ + idx] : T(0),
-              G2 = act ? mc[2 * NQ + idx] : T(0);
+      const T G0 = act ? mc[idx] : T(0), G1 = act ? mc[NQP + idx] : T(0),
+              G2 = act ? mc[2 * NQP + idx] : T(0);
       S(1, idx) = G0 * gx + G1 * gy[q];
       gy[q] = G1 * gx + G2 * gy[q];
     }
@@ -556,22 +588,38 @@ __device__ __forceinline__ void op_reg_unit(const int32_t* __restrict__ cell_nod
   sweep<D, N, kDeriv, false>(B.Dg, v, gx, 0);
   sweep<D, N, kDeriv, false>(B.Dg, v, gy, 1);
   if constexpr (D == 3) sweep<D, N, kDeriv, false>(B.Dg, v, v, 2);  // v now holds d/dz
-  // metric terms: flux = G grad^
-  const T* mc = metric + cell * NM * NQ;
+  // metric terms: flux = G grad^ (FP32 rows loaded four quadrature points at a
+  // time; the FP64-pipe-bound types load one, which keeps their registers)
+  constexpr int NQP = padded_nq(NQ);
+#ifndef NNMG_METRIC_VEC
+#define NNMG_METRIC_VEC 2
+#endif
+  constexpr int W = std::is_same<T, float>::value ? NNMG_METRIC_VEC : 1;
+  const T* mc = metric + cell * NM * NQP;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    if constexpr (D == 3) {
-      const T a = gx[q], b = gy[q], c = v[q];
-      const T G0 = mc[q], G1 = mc[NQ + q], G2 = mc[2 * NQ + q], G3 = mc[3 * NQ + q],
-              G4 = mc[4 * NQ + q], G5 = mc[5 * NQ + q];
-      gx[q] = G0 * a + G1 * b + G2 * c;
-      gy[q] = G1 * a + G3 * b + G4 * c;
-      v[q] = G2 * a + G4 * b + G5 * c;
-    } else {
-      const T a = gx[q], b = gy[q];
-      const T G0 = mc[q], G1 = mc[NQ + q], G2 = mc[2 * NQ + q];
-      gx[q] = G0 * a + G1 * b;
-      gy[q] = G1 * a + G2 * b;
+  for (int q0 = 0; q0 < NQ; q0 += W) {
+    T G[NM][W];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      if constexpr (W > 1)
+        load_metric(mc + m * NQP + q0, G[m]);
+      else
+        G[m][0] = mc[m * NQP + q0];
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const int q = q0 + w;
+      if (q >= NQ) break;
+      if constexpr (D == 3) {
+        const T a = gx[q], b = gy[q], c = v[q];
+        gx[q] = G[0][w] * a + G[1][w] * b + G[2][w] * c;
+        gy[q] = G[1][w] * a + G[3][w] * b + G[4][w] * c;
+        v[q] = G[2][w] * a + G[4][w] * b + G[5][w] * c;
+      } else {
+        const T a = gx[q], b = gy[q];
+        gx[q] = G[0][w] * a + G[1][w] * b;
+        gy[q] = G[1][w] * a + G[2][w] * b;
+      }
     }
   }
   // w = Dx^T fx + Dy^T fy (+ Dz^T fz), then integrate with S^T
@@ -593,7 +641,8 @@ __device__ __forceinline__ void op_reg_unit(const int32_t* __restrict__ cell_nod
 }
 
 template <int D, int K, typename T>
-__global__ void __launch_bounds__(128) op_reg_kernel(const int32_t* __restrict__ cell_nodes,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) op_reg_kernel(
+    const int32_t* __restrict__ cell_nodes,
                                                      const T* __restrict__ metric,
                                                      const typename io_of<T>::type* __restrict__ x,
                                                      typename io_of<T>::type* __restrict__ y,
@@ -756,21 +805,29 @@ __global__ void __launch_bounds__(128) op_reg2_kernel(const int32_t* __restrict_
   sweep<D, N, kDeriv, false>(B.Dg, v, gx, 0);
   sweep<D, N, kDeriv, false>(B.Dg, v, gy, 1);
   if constexpr (D == 3) sweep<D, N, kDeriv, false>(B.Dg, v, v, 2);
-  const float* mc = metric + cell * NM * NQ;
+  constexpr int NQP = padded_nq(NQ);
+  const float* mc = metric + cell * NM * NQP;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    if constexpr (D == 3) {
-      const f2 a = gx[q], b = gy[q], c = v[q];
-      const f2 G0(mc[q]), G1(mc[NQ + q]), G2(mc[2 * NQ + q]), G3(mc[3 * NQ + q]),
-          G4(mc[4 * NQ + q]), G5(mc[5 * NQ + q]);
-      gx[q] = mac(mac(G0 * a, G1, b), G2, c);
-      gy[q] = mac(mac(G1 * a, G3, b), G4, c);
-      v[q] = mac(mac(G2 * a, G4, b), G5, c);
-    } else {
-      const f2 a = gx[q], b = gy[q];
-      const f2 G0(mc[q]), G1(mc[NQ + q]), G2(mc[2 * NQ + q]);
-      gx[q] = mac(G0 * a, G1, b);
-      gy[q] = mac(G1 * a, G2, b);
+  for (int q0 = 0; q0 < NQ; q0 += 4) {
+    float G[NM][4];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) load_metric(mc + m * NQP + q0, G[m]);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int q = q0 + w;
+      if (q >= NQ) break;
+      if constexpr (D == 3) {
+        const f2 a = gx[q], b = gy[q], c = v[q];
+        const f2 G0(G[0][w]), G1(G[1][w]), G2(G[2][w]), G3(G[3][w]), G4(G[4][w]), G5(G[5][w]);
+        gx[q] = mac(mac(G0 * a, G1, b), G2, c);
+        gy[q] = mac(mac(G1 * a, G3, b), G4, c);
+        v[q] = mac(mac(G2 * a, G4, b), G5, c);
+      } else {
+        const f2 a = gx[q], b = gy[q];
+        const f2 G0(G[0][w]), G1(G[1][w]), G2(G[2][w]);
+        gx[q] = mac(G0 * a, G1, b);
+        gy[q] = mac(G1 * a, G2, b);
+      }
     }
   }
   if constexpr (D == 3) {

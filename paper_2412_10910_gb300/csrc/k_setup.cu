@@ -97,7 +97,7 @@ __device__ __forceinline__ void load_corners(const double* __restrict__ vertices
 // stress is K sigma(grad^u K) (Sec. 4.4).
 template <int D>
 __global__ void metric_kernel(const double* __restrict__ vertices, const int32_t* __restrict__ cells,
-                              int64_t nc, int n1, int ncomp, Basis1D<double> B,
+                              int64_t nc, int n1, int ncomp, int nqp, Basis1D<double> B,
                               double* __restrict__ m64, float* __restrict__ m32, int* err) {
   const int nq = D == 2 ? n1 * n1 : n1 * n1 * n1;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,7 +125,7 @@ __global__ void metric_kernel(const double* __restrict__ vertices, const int32_t
         double g = 0.0;
         for (int e = 0; e < D; ++e) g += Ji[a][e] * Ji[b][e];
         g *= dw;
-        const int64_t o = (c * nm + j) * nq + q;
+        const int64_t o = (c * nm + j) * nqp + q;
         m64[o] = g;
         m32[o] = (float)g;
         ++j;
@@ -135,7 +135,7 @@ __global__ void metric_kernel(const double* __restrict__ vertices, const int32_t
     for (int a = 0; a < D; ++a)
       for (int b = 0; b < D; ++b) {
         const double g = s * Ji[a][b];
-        const int64_t o = (c * (D * D) + a * D + b) * nq + q;
+        const int64_t o = (c * (D * D) + a * D + b) * nqp + q;
         m64[o] = g;
         m32[o] = (float)g;
       }
@@ -184,7 +184,7 @@ __global__ void quad_points_kernel(const double* __restrict__ vertices,
 // sum_q lambda h_c^2 + mu (|h|^2 + h_c^2) with h = K^T grad^phi_i.
 template <int D>
 __global__ void diag_kernel(const int32_t* __restrict__ cell_nodes, const double* __restrict__ m64,
-                            int64_t nc, int n1, int ncomp, double lambda, double mu,
+                            int64_t nc, int n1, int ncomp, int nqp, double lambda, double mu,
                             Basis1D<double> B, double* __restrict__ diag) {
   const int nloc = D == 2 ? n1 * n1 : n1 * n1 * n1;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -209,7 +209,7 @@ __global__ void diag_kernel(const int32_t* __restrict__ cell_nodes, const double
       double s = 0.0;
       for (int a = 0; a < D; ++a)
         for (int b = a; b < D; ++b) {
-          const double Gab = m64[(c * nm + j) * nloc + q];
+          const double Gab = m64[(c * nm + j) * nqp + q];
           s += (a == b ? 1.0 : 2.0) * Gab * g[a] * g[b];
           ++j;
         }
@@ -217,7 +217,7 @@ __global__ void diag_kernel(const int32_t* __restrict__ cell_nodes, const double
     } else {
       double h[3] = {0.0, 0.0, 0.0};
       for (int b = 0; b < D; ++b)
-        for (int a = 0; a < D; ++a) h[b] += g[a] * m64[(c * (D * D) + a * D + b) * nloc + q];
+        for (int a = 0; a < D; ++a) h[b] += g[a] * m64[(c * (D * D) + a * D + b) * nqp + q];
       double hh = 0.0;
       for (int b = 0; b < D; ++b) hh += h[b] * h[b];
       for (int e = 0; e < D; ++e) acc[e] += lambda * h[e] * h[e] + mu * (hh + h[e] * h[e]);
@@ -380,10 +380,12 @@ cudaError_t launch_metric(const DevLevel& L, int* d_err, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   if (L.dim == 2)
     metric_kernel<2><<<blocks_for(n, 128), 128, 0, s>>>(L.vertices, L.cells, L.n_cells, L.n1,
-                                                        L.ncomp, b64, L.metric64, L.metric32, d_err);
+                                                        L.ncomp, L.nqp, b64, L.metric64, L.metric32,
+                                                        d_err);
   else
     metric_kernel<3><<<blocks_for(n, 128), 128, 0, s>>>(L.vertices, L.cells, L.n_cells, L.n1,
-                                                        L.ncomp, b64, L.metric64, L.metric32, d_err);
+                                                        L.ncomp, L.nqp, b64, L.metric64, L.metric32,
+                                                        d_err);
   return cudaGetLastError();
 }
 
@@ -422,10 +424,10 @@ cudaError_t launch_diag(const DevLevel& L, double lambda, double mu, cudaStream_
   if (n == 0) return cudaSuccess;
   if (L.dim == 2)
     diag_kernel<2><<<blocks_for(n, 128), 128, 0, s>>>(L.cell_nodes, L.metric64, L.n_cells, L.n1,
-                                                      L.ncomp, lambda, mu, b64, L.diag64);
+                                                      L.ncomp, L.nqp, lambda, mu, b64, L.diag64);
   else
     diag_kernel<3><<<blocks_for(n, 128), 128, 0, s>>>(L.cell_nodes, L.metric64, L.n_cells, L.n1,
-                                                      L.ncomp, lambda, mu, b64, L.diag64);
+                                                      L.ncomp, L.nqp, lambda, mu, b64, L.diag64);
   return cudaGetLastError();
 }
 

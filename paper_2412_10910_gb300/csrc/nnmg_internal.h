@@ -2,9 +2,11 @@
 //
 // Data layout in device memory (one hierarchy):
 //   per level: cell_nodes [n_cells][(k+1)^d] int32 with -1 at Dirichlet nodes;
-//   metric terms per quadrature point, [n_cells][n_metric][(k+1)^d] (component
+//   metric terms per quadrature point, [n_cells][n_metric][nqp] (component
 //   outer, quadrature point inner, so neighbouring threads read neighbouring
-//   words) in FP64 and FP32; inverse Jacobi diagonals per row in FP64 and FP32;
+//   words; rows padded to nqp = (k+1)^d rounded up to a multiple of 4, so a
+//   row starts on a 16-byte boundary and loads as 16-byte vectors) in FP64 and
+//   FP32; inverse Jacobi diagonals per row in FP64 and FP32;
 //   for a level l >= 1 the located fine points sorted by coarse cell
 //   (fine node, reference point) with a CSR start per coarse cell; for a level
 //   used as coarse level the restriction gather list node -> (cell*nloc+local).
@@ -135,6 +137,7 @@ bool dense_spd_inverse(std::vector<double>& a, int n, std::vector<double>* inv);
 // ------------------------------------------------------------ device levels
 struct DevLevel {
   int dim = 0, k = 0, n1 = 0, nloc = 0, ncomp = 1, nmetric = 0;
+  int nqp = 0;                       // metric row stride: nloc rounded up to a multiple of 4
   int64_t n_vertices = 0, n_cells = 0, n_nodes = 0, n_free_nodes = 0, rows = 0;
   HostNumbering num;                 // host numbering (kept for queries)
   std::vector<double> h_vertices;
@@ -144,7 +147,7 @@ struct DevLevel {
   int32_t* cell_nodes = nullptr;     // [nc][nloc], -1 = constrained
   int32_t* owner_cell = nullptr;     // [n_nodes]
   int32_t* owner_local = nullptr;    // [n_nodes]
-  double* metric64 = nullptr;        // [nc][nmetric][nloc]
+  double* metric64 = nullptr;        // [nc][nmetric][nqp], entries nloc..nqp-1 zero
   float* metric32 = nullptr;
   float* metric_dw = nullptr;        // double-word pairs (hi, lo) [nc][nmetric][nloc][2], on demand
   double* diag64 = nullptr;          // [rows] (0 at constrained rows)

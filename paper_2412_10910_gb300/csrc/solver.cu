@@ -155,7 +155,7 @@ int ensure_work(nnmg_handle* h) {
 int ensure_dw(nnmg_handle* h, int level) {
   DevLevel& L = h->lv[level];
   if (L.metric_dw) return NNMG_OK;
-  const size_t nm = (size_t)L.n_cells * L.nmetric * L.nloc;
+  const size_t nm = (size_t)L.n_cells * L.nmetric * L.nqp;
   CK(dalloc(h, &L.metric_dw, 2 * nm));
   CK(launch_split_dw(L.metric64, L.metric_dw, (int64_t)nm, 0));
   CK(cudaStreamSynchronize(0));
@@ -724,6 +724,7 @@ int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStrea
   L.nloc = d.dim == 2 ? L.n1 * L.n1 : L.n1 * L.n1 * L.n1;
   L.ncomp = o.n_components;
   L.nmetric = o.n_components == 1 ? d.dim * (d.dim + 1) / 2 : d.dim * d.dim;
+  L.nqp = (L.nloc + 3) / 4 * 4;
   L.n_vertices = d.n_vertices;
   L.n_cells = d.n_cells;
   const int nc4 = 1 << d.dim;
@@ -762,9 +763,11 @@ int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStrea
   CK(dalloc(h, &L.row_free, (size_t)L.rows));
   CK(cudaMemcpy(L.row_free, rf.data(), L.rows, cudaMemcpyHostToDevice));
   // geometry
-  const size_t nm = (size_t)L.n_cells * L.nmetric * L.nloc;
+  const size_t nm = (size_t)L.n_cells * L.nmetric * L.nqp;
   CK(dalloc(h, &L.metric64, nm));
   CK(dalloc(h, &L.metric32, nm));
+  CK(cudaMemsetAsync(L.metric64, 0, nm * sizeof(double), s));     // the row padding stays zero
+  CK(cudaMemsetAsync(L.metric32, 0, nm * sizeof(float), s));
   int* derr;
   CK(cudaMalloc(&derr, sizeof(int)));
   CK(cudaMemsetAsync(derr, 0, sizeof(int), s));
@@ -974,7 +977,7 @@ size_t planned_hierarchy_bytes(const std::vector<LevelPlan>& P) {
   const int n = (int)P.size();
   for (int l = 0; l < n; ++l) {
     const LevelPlan& L = P[l];
-    const int64_t nm = L.n_cells * L.nmetric * L.nloc;
+    const int64_t nm = L.n_cells * L.nmetric * ((L.nloc + 3) / 4 * 4);
     b += bytes_of<double>(L.n_vertices * L.dim) + bytes_of<int32_t>(L.n_cells << L.dim) +
          bytes_of<int32_t>(L.n_cells * L.nloc) + 2 * bytes_of<int32_t>(L.n_nodes) +
          bytes_of<uint8_t>(L.rows) + bytes_of<double>(nm) + bytes_of<float>(nm) +
