@@ -778,8 +778,11 @@ __global__ void __launch_bounds__(kSmootherThreads) cheb_smoother_kernel(
 // metric load and atomic then serves two right-hand sides, which halves the
 // instruction count of this issue-bound kernel; vectors are read and written
 // as float pairs (8-byte aligned rows of right-hand sides).
+#ifndef NNMG_REG2_MIN_BLOCKS
+#define NNMG_REG2_MIN_BLOCKS 1
+#endif
 template <int D, int K>
-__global__ void __launch_bounds__(128) op_reg2_kernel(const int32_t* __restrict__ cell_nodes,
+__global__ void __launch_bounds__(128, NNMG_REG2_MIN_BLOCKS) op_reg2_kernel(const int32_t* __restrict__ cell_nodes,
                                                       const float* __restrict__ metric,
                                                       const float2* __restrict__ x,
                                                       float2* __restrict__ y, int64_t n_cells,
@@ -840,6 +843,103 @@ __global__ void __launch_bounds__(128) op_reg2_kernel(const int32_t* __restrict_
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) sweep<D, N, kInterp, true>(B.S, v, v, d);
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int dof = cn[i];
+    if (dof >= 0) atomicAdd(&y[(int64_t)dof * npair + pr], v[i].v);
+  }
+}
+
+// Paired FP32 3D form with z-slices streamed: the values at the Gauss points
+// and their z-derivatives are kept for the whole cell, but the x/y gradients
+// and fluxes only for one slice at a time (a slice's values are dead once its
+// gradients and the cell's z-derivatives exist, so its transposed x/y
+// derivatives take their registers).  About 72 live float pairs instead of
+// 81, which fits three 128-thread blocks per SM without spilling.
+#ifndef NNMG_REG2S_MIN_BLOCKS
+#define NNMG_REG2S_MIN_BLOCKS 3
+#endif
+template <int K>
+__global__ void __launch_bounds__(128, NNMG_REG2S_MIN_BLOCKS) op_reg2s_kernel(const int32_t* __restrict__ cell_nodes,
+                                                          const float* __restrict__ metric,
+                                                          const float2* __restrict__ x,
+                                                          float2* __restrict__ y, int64_t n_cells,
+                                                          int npair, Basis1D<f2> B) {
+  pdl_trigger();
+  pdl_wait();
+  constexpr int N = K + 1, N2 = N * N, NQ = N2 * N, NQP = padded_nq(NQ);
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cell = u / npair;
+  if (cell >= n_cells) return;
+  const int pr = (int)(u - cell * npair);
+  const int32_t* cn = cell_nodes + cell * NQ;
+  f2 v[NQ], gz[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int dof = cn[i];
+    v[i] = dof >= 0 ? f2(x[(int64_t)dof * npair + pr]) : f2();
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) sweep<3, N, kInterp, false>(B.S, v, v, d);
+  sweep<3, N, kDeriv, false>(B.Dg, v, gz, 2);
+  const float* mc = metric + cell * 6 * NQP;
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    f2 gx[N2], gy[N2];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {            // x-lines of the slice
+      f2 in[N], out[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) in[i] = v[i + N * j + N2 * c];
+      apply<N, kDeriv>(B.Dg, in, out);
+#pragma unroll
+      for (int i = 0; i < N; ++i) gx[i + N * j] = out[i];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {            // y-lines of the slice
+      f2 in[N], out[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) in[j] = v[i + N * j + N2 * c];
+      apply<N, kDeriv>(B.Dg, in, out);
+#pragma unroll
+      for (int j = 0; j < N; ++j) gy[i + N * j] = out[j];
+    }
+#pragma unroll
+    for (int p = 0; p < N2; ++p) {           // flux = G grad^ at the slice's points
+      const int q = p + N2 * c;
+      const f2 a = gx[p], b = gy[p], cz = gz[q];
+      const f2 G0(mc[q]), G1(mc[NQP + q]), G2(mc[2 * NQP + q]), G3(mc[3 * NQP + q]),
+          G4(mc[4 * NQP + q]), G5(mc[5 * NQP + q]);
+      gx[p] = mac(mac(G0 * a, G1, b), G2, cz);
+      gy[p] = mac(mac(G1 * a, G3, b), G4, cz);
+      gz[q] = mac(mac(G2 * a, G4, b), G5, cz);
+    }
+    // the slice's transposed x and y derivatives replace its values
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      f2 in[N], out[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) in[i] = gx[i + N * j];
+      apply_t<N, kDeriv>(B.Dg, in, out);
+#pragma unroll
+      for (int i = 0; i < N; ++i) v[i + N * j + N2 * c] = out[i];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      f2 in[N], out[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        in[j] = gy[i + N * j];
+        out[j] = v[i + N * j + N2 * c];
+      }
+      apply_t<N, kDeriv, true>(B.Dg, in, out);
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[i + N * j + N2 * c] = out[j];
+    }
+  }
+  sweep<3, N, kDeriv, true, true>(B.Dg, gz, v, 2);   // + transposed z derivative
+#pragma unroll
+  for (int d = 0; d < 3; ++d) sweep<3, N, kInterp, true>(B.S, v, v, d);
 #pragma unroll
   for (int i = 0; i < NQ; ++i) {
     const int dof = cn[i];
@@ -1022,6 +1122,10 @@ cudaError_t run_reg2(const DevLevel& L, const float* metric, const float* x, flo
   pick_basis<f2>(K, &B);
   const int npair = nrhs / 2;
   const int64_t units = L.n_cells * npair;
+  if constexpr (D == 3)
+    return launch_k(op_reg2s_kernel<K>, (unsigned)((units + 127) / 128), 128, 0, s, L.cell_nodes,
+                    metric, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y),
+                    L.n_cells, npair, B);
   return launch_k(op_reg2_kernel<D, K>, (unsigned)((units + 127) / 128), 128, 0, s, L.cell_nodes,
                   metric, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), L.n_cells,
                   npair, B);

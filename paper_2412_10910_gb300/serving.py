@@ -177,8 +177,10 @@ class Server:
     """Admits requests by device-memory budget and runs all families' engines."""
 
     def __init__(self, families: dict, budget_bytes: int, nslots=16, mode=_abi.FP32_MG_FP64_CG,
-                 rtol=1e-8, maxit=200, engine_factory=None):
+                 rtol=1e-8, maxit=200, engine_factory=None, poll_pause_s=0.0):
         self.families = families
+        # pause between polls while steps are in flight (0: poll continuously)
+        self.poll_pause_s = poll_pause_s
         self.budget = budget_bytes
         self.kw = dict(nslots=nslots, mode=mode, rtol=rtol, maxit=maxit)
         self.engines: dict[str, FamilyEngine] = {}
@@ -264,6 +266,8 @@ class Server:
                 inflight = [e for e in self.engines.values() if e.inflight]
                 if inflight and not pending and not waiting:
                     inflight[0].stream.synchronize()
+                elif inflight and self.poll_pause_s > 0:
+                    time.sleep(self.poll_pause_s)
                 elif not inflight and pending and not waiting and \
                         not any(e.busy() for e in self.engines.values()):
                     dt = pending[0].arrival * time_scale - (time.perf_counter() - t0)
