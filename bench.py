@@ -559,7 +559,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["solve", "solve64", "solvedw", "vcycle", "op64", "op32",
-                                       "opdw", "serving", "configs", "peaks"],
+                                       "opdw", "prolong", "restrict", "serving", "configs", "peaks"],
                     default=None, help="run only one timed section (for profiler launch lists), "
                     "or the serving mix")
     ap.add_argument("--requests", type=int, default=2000, help="serving mix: number of requests")
@@ -630,6 +630,13 @@ def main():
             r32 = torch.randn(rows, nrhs, dtype=torch.float32, device="cuda")
             z32 = torch.empty_like(r32)
             fns["vcycle"] = lambda: H.vcycle(r32, z32)
+        if args.only in ("prolong", "restrict"):
+            # the finest pair's FP32 transfers (nnmg_prolongate zeroes the fine
+            # vector first; nnmg_restrict runs both phases)
+            xc = torch.randn(H.rows(top - 1), nrhs, device="cuda")
+            xf = torch.randn(rows, nrhs, device="cuda")
+            fns["prolong"] = lambda: H.prolongate(top, xc, xf)
+            fns["restrict"] = lambda: H.restrict(top, xf, xc)
         if args.only in ("op64", "op32", "opdw"):
             dt = torch.float32 if args.only == "op32" else torch.float64
             xo = torch.randn(rows, nrhs, dtype=dt, device="cuda")
