@@ -97,26 +97,34 @@ __global__ void __launch_bounds__(128, F == 1 ? NNMG_RESTRICT_MIN_BLOCKS : 4) re
           for (int b = 0; b < kLanePts; ++b)
             if (node[b] >= 0) load_group<T, CH>(rf + (int64_t)node[b] * nch + gg * CH, v[b]);
           if (tres) {
-            // fused residual: r = f - t at the point's row, and t = 0 there in
-            // the last round over the points (every free fine node is exactly
-            // one point, so all of t is reset; earlier rounds still read t)
-            P tv[kLanePts][NP], zero[NP];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) zero[q] = pzero(P());
+            // fused residual: r = f - t at the point's row
+            P tv[kLanePts][NP];
 #pragma unroll
             for (int b = 0; b < kLanePts; ++b)
               if (node[b] >= 0) load_group<T, CH>(tres + (int64_t)node[b] * nch + gg * CH, tv[b]);
 #pragma unroll
             for (int b = 0; b < kLanePts; ++b)
-              if (node[b] >= 0) {
+              if (node[b] >= 0)
 #pragma unroll
                 for (int q = 0; q < NP; ++q) v[b][q] = psub(v[b][q], tv[b][q]);
-                if (rd == rounds - 1) store_group<T, CH>(tres + (int64_t)node[b] * nch + gg * CH, zero);
-              }
           }
 #pragma unroll
           for (int b = 0; b < kLanePts; ++b)
             if (node[b] >= 0) store_group<T, CH>(sr + (lane + 32 * b) * nch + gg * CH, v[b]);
+        }
+        if (tres && rd == rounds - 1) {
+          // t = 0 at the points' rows, in the last round over the points (every
+          // free fine node is exactly one point, so all of t is reset; earlier
+          // rounds still read t).  The stores follow all of this round's
+          // loads: a global store between them would serialise their round
+          // trips (the rows of t may alias as far as the compiler knows).
+          P zero[NP];
+#pragma unroll
+          for (int q = 0; q < NP; ++q) zero[q] = pzero(P());
+          for (int gg = 0; gg < ng; ++gg)
+#pragma unroll
+            for (int b = 0; b < kLanePts; ++b)
+              if (node[b] >= 0) store_group<T, CH>(tres + (int64_t)node[b] * nch + gg * CH, zero);
         }
 #pragma unroll
         for (int b = 0; b < kLanePts; ++b)

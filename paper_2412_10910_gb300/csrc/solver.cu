@@ -302,6 +302,11 @@ void drop_graphs(nnmg_handle* h) {
   h->loops.clear();
 }
 
+bool fused_residual_allowed() {
+  const char* e = getenv("NNMG_FUSED_RESIDUAL");    // read when a V-cycle is enqueued or captured
+  return !(e && e[0] == '0');
+}
+
 int* smoother_err(nnmg_handle* h) {
   return h->smoother_sync ? reinterpret_cast<int*>(h->smoother_sync + 2) : nullptr;
 }
@@ -396,9 +401,16 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
       RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_OPERATOR,
           launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
     }
-    // r_l = f_l - A_l x_l formed inside the restriction (t reset to zero there)
-    RUN(l, NNMG_PROF_RESTRICT, NNMG_PROF_RESTRICT,
-        launch_restrict_residual<T>(L, h->lv[l - 1], f, t, d, W.f[l - 1], W.scratch[l], nrhs, s));
+    // r_l = f_l - A_l x_l formed inside the restriction (t reset to zero there);
+    // NNMG_FUSED_RESIDUAL=0 runs the residual kernel and the plain restriction
+    if (fused_residual_allowed()) {
+      RUN(l, NNMG_PROF_RESTRICT, NNMG_PROF_RESTRICT,
+          launch_restrict_residual<T>(L, h->lv[l - 1], f, t, d, W.f[l - 1], W.scratch[l], nrhs, s));
+    } else {
+      RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_VECTOR, launch_residual<T>(f, t, d, L.rows, nrhs, s));
+      RUN(l, NNMG_PROF_RESTRICT, NNMG_PROF_RESTRICT,
+          launch_restrict<T>(L, h->lv[l - 1], d, W.f[l - 1], W.scratch[l], nrhs, s));
+    }
   }
   {
     const T* f0 = top == 0 ? f_top : W.f[0];
