@@ -41,11 +41,11 @@ FP64_PIPE_TOPS = 152 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per (cell, right-hand side) of the FP64 fine-level operator, from
 # ncu's dram__bytes_read.sum + dram__bytes_write.sum of one launch on config 2
-# (412.6 + 65.7 MB over 166,375 cells x 8 RHS, padded metric rows), keyed by
+# (412.5 + 66.8 MB over 166,375 cells x 8 RHS, padded metric rows), keyed by
 # the kernel choice the counters were taken on (-1: op_reg_kernel<3,2,double>).
 # The launch's traffic is this times its cells x RHS; another choice reports
 # null.
-OP64_TRAFFIC_PER_UNIT = {-1: (412615168 + 65718272) / (166375 * 8)}
+OP64_TRAFFIC_PER_UNIT = {-1: (412489472 + 66762496) / (166375 * 8)}
 
 
 def op64_traffic(choice, n_cells, nrhs):
