@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnnmg.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["host_setup.cpp", "k_setup.cu", "k_operator.cu", "k_transfer.cu", "k_prolong.cu",
-           "k_restrict.cu", "k_vector.cu", "solver.cu", "noalloc.cu", "probe.cu"]
+           "k_restrict.cu", "k_vector.cu", "k_dense.cu", "solver.cu", "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

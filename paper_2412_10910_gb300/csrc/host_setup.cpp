@@ -1,9 +1,7 @@
 // Host-side setup: 1D basis tables, continuous Q_k node numbering, Dirichlet
-// set, coarse-cell bucket grid for point location and the dense FP64
-// factorisation of the coarsest operator.
+// set and the coarse-cell bucket grid for point location.
 #include <algorithm>
 #include <cmath>
-#include <thread>
 
 #include "nnmg_internal.h"
 
@@ -443,133 +441,6 @@ void build_buckets(const double* vertices, const int32_t* cells, int64_t nc, int
           }
     }
   }
-}
-
-// ------------------------------------------------------------ dense SPD
-// Blocked right-looking Cholesky A = L L^T (lower, row-major) with the
-// trailing update split over host threads; then W = L^-1 and A^-1 = W^T W.
-// Both products run on 32-column blocks of W whose rows are contiguous, so
-// the inner loops are vectorizable updates over a block's columns that reuse
-// each loaded factor entry 32 times.
-bool dense_spd_inverse(std::vector<double>& a, int n, std::vector<double>* inv) {
-  const int nb = 64;
-  unsigned nt = std::max(1u, std::thread::hardware_concurrency());
-  auto par = [&](int64_t lo, int64_t hi, auto fn) {
-    int64_t m = hi - lo;
-    if (m <= 0) return;
-    unsigned t = (unsigned)std::min<int64_t>(nt, m);
-    std::vector<std::thread> th;
-    for (unsigned i = 0; i < t; ++i) {
-      th.emplace_back([&, i]() {
-        for (int64_t r = lo + i; r < hi; r += t) fn(r);
-      });
-    }
-    for (auto& x : th) x.join();
-  };
-  double* A = a.data();
-  for (int k0 = 0; k0 < n; k0 += nb) {
-    int k1 = std::min(n, k0 + nb);
-    // factor the diagonal block
-    for (int j = k0; j < k1; ++j) {
-      double s = A[(size_t)j * n + j];
-      for (int p = k0; p < j; ++p) s -= A[(size_t)j * n + p] * A[(size_t)j * n + p];
-      if (!(s > 0.0)) return false;
-      double ljj = std::sqrt(s);
-      A[(size_t)j * n + j] = ljj;
-      for (int i = j + 1; i < k1; ++i) {
-        double t = A[(size_t)i * n + j];
-        for (int p = k0; p < j; ++p) t -= A[(size_t)i * n + p] * A[(size_t)j * n + p];
-        A[(size_t)i * n + j] = t / ljj;
-      }
-    }
-    // panel below: L21 = A21 L11^-T
-    par(k1, n, [&](int64_t i) {
-      double* ri = A + (size_t)i * n;
-      for (int j = k0; j < k1; ++j) {
-        double t = ri[j];
-        const double* rj = A + (size_t)j * n;
-        for (int p = k0; p < j; ++p) t -= ri[p] * rj[p];
-        ri[j] = t / rj[j];
-      }
-    });
-    // trailing update A22 -= L21 L21^T (lower triangle) in 4 x 4 blocks of
-    // rows: every loaded panel entry feeds four multiply-adds
-    const int nrb = (n - k1 + 3) / 4;
-    par(0, nrb, [&](int64_t ib) {
-      const int i0 = k1 + 4 * (int)ib, ni = std::min(4, n - i0);
-      const double* xr[4];
-      for (int r = 0; r < 4; ++r) xr[r] = A + (size_t)(i0 + std::min(r, ni - 1)) * n;
-      for (int j0 = k1; j0 < i0 + ni; j0 += 4) {
-        const int nj = std::min(4, n - j0);
-        const double* yr[4];
-        for (int c = 0; c < 4; ++c) yr[c] = A + (size_t)(j0 + std::min(c, nj - 1)) * n;
-        double acc[4][4] = {{0.0}};
-        for (int p = k0; p < k1; ++p) {
-          const double x0 = xr[0][p], x1 = xr[1][p], x2 = xr[2][p], x3 = xr[3][p];
-          const double y[4] = {yr[0][p], yr[1][p], yr[2][p], yr[3][p]};
-          for (int c = 0; c < 4; ++c) {
-            acc[0][c] += x0 * y[c];
-            acc[1][c] += x1 * y[c];
-            acc[2][c] += x2 * y[c];
-            acc[3][c] += x3 * y[c];
-          }
-        }
-        for (int r = 0; r < ni; ++r)
-          for (int c = 0; c < nj; ++c)
-            if (j0 + c <= i0 + r) A[(size_t)(i0 + r) * n + j0 + c] -= acc[r][c];
-      }
-    });
-  }
-  // W = L^-1 by blocks of B columns: block jb holds rows jb*B .. n-1 (rows
-  // above are zero), W[i][j] = (delta_ij - sum_{p<i} L[i][p] W[p][j]) / L[i][i]
-  constexpr int B = 32;
-  const int nblk = (n + B - 1) / B;
-  std::vector<std::vector<double>> Wb((size_t)nblk);
-  par(0, nblk, [&](int64_t jb) {
-    const int c0 = (int)jb * B, w = std::min(B, n - c0);
-    std::vector<double>& W = Wb[(size_t)jb];
-    W.assign((size_t)(n - c0) * B, 0.0);
-    for (int i = c0; i < n; ++i) {
-      double acc[B];                          // row i of the block, kept in registers
-      for (int j = 0; j < B; ++j) acc[j] = (i - c0 == j && j < w) ? 1.0 : 0.0;
-      const double* li = A + (size_t)i * n;
-      for (int p = c0; p < i; ++p) {
-        const double l = li[p];
-        const double* wp = &W[(size_t)(p - c0) * B];
-        for (int j = 0; j < B; ++j) acc[j] -= l * wp[j];
-      }
-      double* wi = &W[(size_t)(i - c0) * B];
-      const double d = li[i];
-      for (int j = 0; j < B; ++j) wi[j] = acc[j] / d;
-    }
-  });
-  // A^-1 = W^T W: block (ja, jb), ja <= jb, sums rows i >= jb*B; mirrored
-  std::vector<std::pair<int, int>> pairs;
-  for (int jb = 0; jb < nblk; ++jb)
-    for (int ja = 0; ja <= jb; ++ja) pairs.emplace_back(ja, jb);
-  inv->assign((size_t)n * n, 0.0);
-  par(0, (int64_t)pairs.size(), [&](int64_t t) {
-    const int ja = pairs[(size_t)t].first, jb = pairs[(size_t)t].second;
-    double acc[B][B];
-    for (int a = 0; a < B; ++a)
-      for (int b = 0; b < B; ++b) acc[a][b] = 0.0;
-    for (int i = jb * B; i < n; ++i) {
-      const double* wa = &Wb[(size_t)ja][(size_t)(i - ja * B) * B];
-      const double* wb = &Wb[(size_t)jb][(size_t)(i - jb * B) * B];
-      for (int a = 0; a < B; ++a) {
-        const double x = wa[a];
-        for (int b = 0; b < B; ++b) acc[a][b] += x * wb[b];
-      }
-    }
-    const int na = std::min(B, n - ja * B), nbb = std::min(B, n - jb * B);
-    for (int a = 0; a < na; ++a)
-      for (int b = 0; b < nbb; ++b) {
-        const int r = ja * B + a, c = jb * B + b;
-        (*inv)[(size_t)r * n + c] = acc[a][b];
-        (*inv)[(size_t)c * n + r] = acc[a][b];
-      }
-  });
-  return true;
 }
 
 }  // namespace nnmg

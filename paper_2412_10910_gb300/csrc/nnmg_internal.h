@@ -130,9 +130,7 @@ struct BucketGrid {
 void build_buckets(const double* vertices, const int32_t* cells, int64_t nc, int dim,
                    BucketGrid* g, std::vector<double>* aabb);
 
-// Dense SPD factorisation and inverse on the host (FP64): inv = A^-1.
-// Returns false if a pivot is not positive.
-bool dense_spd_inverse(std::vector<double>& a, int n, std::vector<double>* inv);
+
 
 // ------------------------------------------------------------ device levels
 struct DevLevel {
@@ -234,6 +232,12 @@ cudaError_t launch_restrict_gather(const DevLevel& coarse, const T* scratch, T* 
                                    cudaStream_t s);
 template <typename TI, typename TO>
 cudaError_t launch_coarse_solve(const DevLevel& L, const TI* r, TO* z, int nrhs, cudaStream_t s);
+// The free-row block of level L's operator into D [n][n] and its inverse in
+// place (n = L.n_free_rows; blocked Gauss-Jordan, FP64).  X, Y: L.rows x
+// kMaxRhs doubles; work: n x 64 + 64 x 64 doubles; *err set to 1 on a
+// non-positive pivot.  Enqueued on s.
+cudaError_t launch_coarse_inverse(const DevLevel& L, double lambda, double mu, double* D, double* X,
+                                  double* Y, double* work, int* err, cudaStream_t s);
 
 // One Chebyshev-Jacobi smoothing sweep as a single persistent (cooperative)
 // kernel for small levels served by the register operator (Poisson, 3D k <= 2,

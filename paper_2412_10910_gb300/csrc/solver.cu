@@ -672,6 +672,8 @@ int lanczos(nnmg_handle* h, DevLevel& L, cudaStream_t s) {
   return NNMG_OK;
 }
 
+// The coarsest level's direct solve: the dense free-row block of its operator
+// and the inverse, both built on the device (k_dense.cu).
 int setup_coarse(nnmg_handle* h, DevLevel& L, cudaStream_t s) {
   std::vector<int32_t> rows;
   for (int64_t r = 0; r < L.rows; ++r)
@@ -681,50 +683,32 @@ int setup_coarse(nnmg_handle* h, DevLevel& L, cudaStream_t s) {
   CK(dalloc(h, &L.free_rows, std::max(n, 1)));
   if (n == 0) return NNMG_OK;
   CK(cudaMemcpy(L.free_rows, rows.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
-  std::vector<double> A((size_t)n * n, 0.0);
-  const int nb = kMaxRhs;
-  double *X, *Y;
-  CK(cudaMalloc(&X, (size_t)L.rows * nb * sizeof(double)));
-  CK(cudaMalloc(&Y, (size_t)L.rows * nb * sizeof(double)));
-  std::vector<double> hx((size_t)L.rows * nb), hy((size_t)L.rows * nb);
-  int rc = NNMG_OK;
-  for (int j0 = 0; j0 < n && rc == NNMG_OK; j0 += nb) {
-    const int m = std::min(nb, n - j0);
-    std::fill(hx.begin(), hx.end(), 0.0);
-    for (int c = 0; c < m; ++c) hx[(size_t)rows[j0 + c] * m + c] = 1.0;
-    cudaError_t e = cudaMemcpyAsync(X, hx.data(), (size_t)L.rows * m * sizeof(double),
-                                    cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(Y, 0, (size_t)L.rows * m * sizeof(double), s);
-    if (e == cudaSuccess) e = launch_operator<double>(L, X, Y, m, h->opt.lambda, h->opt.mu, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(hy.data(), Y, (size_t)L.rows * m * sizeof(double),
-                          cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      set_error(std::string("coarse assembly: ") + cudaGetErrorString(e));
-      rc = NNMG_CUDA_ERROR;
-      break;
-    }
-    for (int i = 0; i < n; ++i)
-      for (int c = 0; c < m; ++c) A[(size_t)i * n + j0 + c] = hy[(size_t)rows[i] * m + c];
-  }
+  CK(dalloc(h, &L.coarse_inv, (size_t)n * n));
+  CK(dalloc(h, &L.coarse_partial, (size_t)kCoarseMaxSegments * n * kMaxRhs));
+  double *X = nullptr, *Y = nullptr, *work = nullptr;
+  int* err = nullptr;
+  int herr = 0;
+  cudaError_t e = cudaMalloc(&X, (size_t)L.rows * kMaxRhs * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&Y, (size_t)L.rows * kMaxRhs * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&work, ((size_t)n * 64 + 64 * 64) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = launch_coarse_inverse(L, h->opt.lambda, h->opt.mu, L.coarse_inv, X, Y, work, err, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(X);
   cudaFree(Y);
-  if (rc != NNMG_OK) return rc;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < i; ++j) {
-      const double v = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
-      A[(size_t)i * n + j] = v;
-      A[(size_t)j * n + i] = v;
-    }
-  std::vector<double> inv;
-  if (!dense_spd_inverse(A, n, &inv)) {
+  cudaFree(work);
+  cudaFree(err);
+  if (e != cudaSuccess) {
+    set_error(std::string("coarse inverse: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? NNMG_OUT_OF_MEMORY : NNMG_CUDA_ERROR;
+  }
+  if (herr) {
     set_error("coarsest operator is not positive definite");
     return NNMG_CHOLESKY_FAIL;
   }
-  CK(dalloc(h, &L.coarse_inv, (size_t)n * n));
-  CK(dalloc(h, &L.coarse_partial, (size_t)kCoarseMaxSegments * n * kMaxRhs));
-  CK(cudaMemcpy(L.coarse_inv, inv.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice));
   return NNMG_OK;
 }
 
