@@ -473,6 +473,7 @@ def run_nested_cube(args, rank):
 
 def run_serving(args, rank):
     """Serving mix: 12 cached mesh families, Poisson arrivals, continuous batching."""
+    import numpy as np
     import torch
     from paper_2412_10910_gb300.serving import FamilySpec, Request, Server, latency_stats
     from synthetic.serving import request_rhs, serving_families, serving_requests
@@ -498,18 +499,37 @@ def run_serving(args, rank):
     t = time.perf_counter()
     server.run(cal)
     cal_rate = ncal / (time.perf_counter() - t)
-    rate = 0.8 * cal_rate
+    rate = args.rate if args.rate else 0.8 * cal_rate
+    for e in server.engines.values():          # occupancy of the timed run only
+        e.iterations = e.column_iterations = e.width_iterations = 0
+        e.host_copy_s = 0.0
     reqs = make(serving_requests(fams, args.requests, seed=6, rate=rate))
     t = time.perf_counter()
     done = server.run(reqs)
     span = time.perf_counter() - t
     dofs = sum(next(f for f in fams if f["name"] == r.family)["n_free"] * r.nrhs for r in done)
     ok = all(all(s == 0 for s in r.status) and max(r.relres) <= 1e-8 for r in done)
+    per_family = {}
+    for f in fams:
+        mine = [r for r in done if r.family == f["name"]]
+        eng = server.engines.get(f["name"])
+        if not mine:
+            continue
+        lat = np.array([r.t_done - r.arrival for r in mine])
+        per_family[f["name"]] = {
+            "requests": len(mine), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)),
+            # occupied slots per iteration / 16, and per column the batch computed
+            "slot_occupancy": (eng.column_iterations / max(1, eng.iterations * eng.nslots)
+                               if eng is not None else None),
+            "occupied_per_computed_column": (eng.column_iterations / max(1, eng.width_iterations)
+                                             if eng is not None else None),
+            "host_copy_s": eng.host_copy_s if eng is not None else None}
     line = {"metric": "serving: solved DoF/s and p50/p99 request latency", "value": dofs / span,
             "unit": UNIT, "requests": len(done), "arrival_rate_per_s": rate,
             "calibration_rate_per_s": cal_rate, "makespan_s": span,
             "latency": latency_stats(done), "all_converged": ok, "setup_s_12_families": setup_s,
-            "evictions": server.evictions, "budget_bytes": budget,
+            "evictions": server.evictions, "budget_bytes": budget, "per_family": per_family,
             "families": [f["name"] for f in fams], "data": "synthetic",
             "config": {"workload": "serving mix: 12 jittered non-nested families (seed 5), "
                                    "Poisson arrivals (seed 6), 1-16 N(0,1) RHS, FP32 V-cycle / "
@@ -564,6 +584,8 @@ def main():
                     default=None, help="run only one timed section (for profiler launch lists), "
                     "or the serving mix")
     ap.add_argument("--requests", type=int, default=2000, help="serving mix: number of requests")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="serving mix: arrivals per second (default 0.8 x the calibrated rate)")
     ap.add_argument("--config", default=CONFIG, choices=["c1_2d_q1", "c2_3d_q2", "c3_3d_q4_deformed"],
                     help="Poisson configuration of the --only sections (the full line always "
                          "measures config 2)")

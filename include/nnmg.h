@@ -327,6 +327,10 @@ int nnmg_pcg_solve_host(nnmg_handle* h, int mode, const double* b_host, double* 
  *   column ||r|| <= rtol ||b||) and maxit (per column) as for nnmg_pcg_solve.
  * nnmg_batch_admit: start column `slot` from the FP64 right-hand side b [rows]
  *   (device, or host if b_on_host) with x0 = 0.
+ * nnmg_batch_admit_cols: start columns first_slot .. first_slot + ncols - 1
+ *   from columns 0 .. ncols - 1 of b [rows][ldb] (row-major, ldb >= ncols;
+ *   device, or host if b_on_host with ldb <= max_nrhs: one contiguous copy of
+ *   rows x ldb values, then the columns are spread on the device).
  * nnmg_batch_step: enqueue `iterations` PCG iterations of all columns
  *   (inactive columns stay frozen; a column that converges stops updating)
  *   and an asynchronous copy of the per-column state.
@@ -337,13 +341,25 @@ int nnmg_pcg_solve_host(nnmg_handle* h, int mode, const double* b_host, double* 
  * nnmg_batch_retire: enqueue the copy of column `slot` of x into x [rows]
  *   (device, or host if x_on_host; host memory should be pinned) and mark the
  *   slot empty.  The copy is asynchronous: read x after synchronising the
- *   stream or after the next nnmg_batch_poll that reports ready. */
+ *   stream or after the next nnmg_batch_poll that reports ready.
+ * nnmg_batch_repack: change the batch to new_slots (1..max_nrhs) columns;
+ *   column j < new_slots continues old column src[j] (host array of
+ *   new_slots entries, distinct old slots or -1 for an empty column) with
+ *   its iterate, residual, search direction and scalars unchanged; old
+ *   columns not listed are dropped (retire them first).  Every later step
+ *   costs in proportion to new_slots, so a server keeps the occupied columns
+ *   packed into a batch no wider than it needs.  Call only when no step is
+ *   in flight (after nnmg_batch_poll reported ready); enqueued on `stream`,
+ *   no allocation.  Errors: INVALID_ARG, CUDA_ERROR. */
 int nnmg_batch_reset(nnmg_handle* h, int mode, int nslots, double rtol, int maxit, void* stream);
 int nnmg_batch_admit(nnmg_handle* h, int slot, const double* b, int b_on_host, void* stream);
+int nnmg_batch_admit_cols(nnmg_handle* h, int first_slot, int ncols, const double* b, int ldb,
+                          int b_on_host, void* stream);
 int nnmg_batch_step(nnmg_handle* h, int iterations, void* stream);
 int nnmg_batch_poll(nnmg_handle* h, int wait, int* ready, int* active, int* iters,
                     double* relres, int* status);
 int nnmg_batch_retire(nnmg_handle* h, int slot, double* x, int x_on_host, void* stream);
+int nnmg_batch_repack(nnmg_handle* h, int new_slots, const int* src, void* stream);
 
 /* Arithmetic pipe rate of the current GPU (no counterpart in the paper: the
  * denominator of the rooflines of ALU-bound kernels).  Runs independent

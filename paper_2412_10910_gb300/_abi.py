@@ -74,6 +74,9 @@ PROTOTYPES = {
     "nnmg_batch_poll": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "nnmg_batch_retire": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    "nnmg_batch_admit_cols": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                        C.c_void_p]),
+    "nnmg_batch_repack": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "nnmg_pipe_rate": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "nnmg_last_error": (C.c_char_p, []),
 }

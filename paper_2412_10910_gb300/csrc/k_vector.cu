@@ -224,31 +224,111 @@ __global__ void batch_reset_kernel(PcgScalars* sc, double rtol, int maxit) {
   }
 }
 
-// Column `slot` of [rows][nslots] vectors: r = b on free rows, x = p = 0;
-// partial sums of ||b||^2 for batch_admit_scalar_kernel.
+// Columns first_slot .. first_slot + ncols - 1 of the [rows][nslots] batch
+// vectors start from columns 0 .. ncols - 1 of b [rows][ldb]: r = b on free
+// rows, x = p = 0; partial sums of ||b||^2 per column.  A thread keeps one
+// column (threadIdx.x mod ncols) and strides over rows.
 __global__ void __launch_bounds__(kDotThreads) batch_admit_kernel(
-    const double* __restrict__ b, const uint8_t* __restrict__ row_free, double* __restrict__ r,
-    float* __restrict__ r32, double* __restrict__ x, double* __restrict__ p,
-    double* __restrict__ partial, int64_t rows, int nslots, int slot) {
+    const double* __restrict__ b, int ldb, const uint8_t* __restrict__ row_free,
+    double* __restrict__ r, float* __restrict__ r32, double* __restrict__ x, double* __restrict__ p,
+    double* __restrict__ partial, int64_t rows, int nslots, int first_slot, int ncols) {
+  const unsigned act = dot_threads(ncols);
+  const int64_t per_block = act / ncols;
   double v = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double bv = row_free[i] ? b[i] : 0.0;
-    const int64_t e = i * nslots + slot;
-    r[e] = bv;
-    r32[e] = (float)bv;
-    x[e] = 0.0;
-    p[e] = 0.0;
-    v += bv * bv;
+  if (threadIdx.x < act) {
+    const int c = threadIdx.x % ncols;
+    for (int64_t i = blockIdx.x * per_block + threadIdx.x / ncols; i < rows;
+         i += (int64_t)gridDim.x * per_block) {
+      const double bv = row_free[i] ? b[i * ldb + c] : 0.0;
+      const int64_t e = i * nslots + first_slot + c;
+      r[e] = bv;
+      r32[e] = (float)bv;
+      x[e] = 0.0;
+      p[e] = 0.0;
+      v += bv * bv;
+    }
   }
-  block_store_partials(v, 1, partial);
+  block_store_partials(v, ncols, partial);
 }
 
-__global__ void batch_admit_scalar_kernel(PcgScalars* sc, const double* partial, int slot) {
-  const double bn = sqrt(sum_partials_warp(partial, 0));
+// One warp per admitted column: ||b|| and the column's start state.
+__global__ void batch_admit_scalar_kernel(PcgScalars* sc, const double* partial, int first_slot,
+                                          int ncols) {
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (c < ncols) {
+    const double bn = sqrt(sum_partials_warp(partial, c));
+    if (lane == 0) start_column(sc, first_slot + c, bn, true);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    start_column(sc, slot, bn, true);
-    sc->any_active |= sc->active[slot];
+    int any = sc->any_active;
+    for (int j = 0; j < ncols; ++j) any |= sc->active[first_slot + j];
+    sc->any_active = any;
+  }
+}
+
+// out [rows] = column `slot` of v [rows][nslots].
+__global__ void column_gather_kernel(const double* __restrict__ v, double* __restrict__ out,
+                                     int64_t rows, int nslots, int slot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = v[i * nslots + slot];
+}
+
+// Repacking a batch: column j < new_slots of [rows][new_slots] takes column
+// m.s[j] of [rows][old_slots] (zero where m.s[j] < 0); out32, if given,
+// receives the same values rounded to FP32.
+__global__ void __launch_bounds__(kDotThreads) batch_repack_vec_kernel(
+    const double* __restrict__ in, double* __restrict__ out, float* __restrict__ out32,
+    int64_t rows, int old_slots, int new_slots, SlotMap m) {
+  const int64_t n = rows * new_slots;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / new_slots;
+    const int q = m.s[e - i * new_slots];
+    const double v = q >= 0 ? in[i * old_slots + q] : 0.0;
+    out[e] = v;
+    if (out32) out32[e] = (float)v;
+  }
+}
+
+// The per-column PCG state follows its column; new empty columns start
+// inactive.  One thread per column.
+__global__ void batch_repack_scalar_kernel(PcgScalars* sc, int new_slots, SlotMap m) {
+  __shared__ int act[kMaxRhs];
+  const int j = threadIdx.x;
+  const int q = j < new_slots ? m.s[j] : -1;
+  double rho = 0.0, alpha = 0.0, beta = 0.0, bn = 0.0, rn = 0.0;
+  int a = 0, it = 0, first = 1, failed = 0, broken = 0;
+  if (q >= 0) {
+    rho = sc->rho[q];
+    alpha = sc->alpha[q];
+    beta = sc->beta[q];
+    bn = sc->bnorm[q];
+    rn = sc->rnorm[q];
+    a = sc->active[q];
+    it = sc->iters[q];
+    first = sc->first[q];
+    failed = sc->failed[q];
+    broken = sc->broken[q];
+  }
+  __syncthreads();
+  sc->rho[j] = rho;
+  sc->alpha[j] = alpha;
+  sc->beta[j] = beta;
+  sc->bnorm[j] = bn;
+  sc->rnorm[j] = rn;
+  sc->active[j] = a;
+  sc->iters[j] = it;
+  sc->first[j] = first;
+  sc->failed[j] = failed;
+  sc->broken[j] = broken;
+  act[j] = a;
+  __syncthreads();
+  if (j == 0) {
+    int any = 0;
+    for (int c = 0; c < kMaxRhs; ++c) any |= act[c];
+    sc->any_active = any;
   }
 }
 
@@ -499,14 +579,38 @@ cudaError_t launch_batch_reset(PcgScalars* sc, double rtol, int maxit, cudaStrea
   batch_reset_kernel<<<1, 32, 0, s>>>(sc, rtol, maxit);
   return cudaGetLastError();
 }
-cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double* r, float* r32,
-                               double* x, double* p, double* partial, PcgScalars* sc,
-                               int64_t rows, int nslots, int slot, cudaStream_t s) {
-  batch_admit_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, row_free, r, r32, x, p, partial, rows,
-                                                       nslots, slot);
+cudaError_t launch_batch_admit(const double* b, int ldb, const uint8_t* row_free, double* r,
+                               float* r32, double* x, double* p, double* partial, PcgScalars* sc,
+                               int64_t rows, int nslots, int first_slot, int ncols, cudaStream_t s) {
+  batch_admit_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(b, ldb, row_free, r, r32, x, p, partial,
+                                                       rows, nslots, first_slot, ncols);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  batch_admit_scalar_kernel<<<1, 32, 0, s>>>(sc, partial, slot);
+  batch_admit_scalar_kernel<<<1, 32 * kMaxRhs, 0, s>>>(sc, partial, first_slot, ncols);
+  return cudaGetLastError();
+}
+cudaError_t launch_column_gather(const double* v, double* out, int64_t rows, int nslots, int slot,
+                                 cudaStream_t s) {
+  column_gather_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(v, out, rows, nslots, slot);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_repack(double* x, double* r, float* r32, double* p, double* tmp,
+                                PcgScalars* sc, int64_t rows, int old_slots, int new_slots,
+                                const SlotMap& m, cudaStream_t s) {
+  const size_t bytes = (size_t)rows * new_slots * sizeof(double);
+  double* vec[3] = {x, r, p};
+  for (int v = 0; v < 3; ++v) {
+    batch_repack_vec_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(vec[v], tmp, v == 1 ? r32 : nullptr,
+                                                               rows, old_slots, new_slots, m);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vec[v], tmp, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  // tmp is the operator's output A p, which is zero between iterations (the
+  // operator adds into it)
+  cudaError_t e = cudaMemsetAsync(tmp, 0, bytes, s);
+  if (e != cudaSuccess) return e;
+  batch_repack_scalar_kernel<<<1, kMaxRhs, 0, s>>>(sc, new_slots, m);
   return cudaGetLastError();
 }
 template <typename TZ>

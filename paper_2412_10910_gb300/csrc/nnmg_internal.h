@@ -306,9 +306,24 @@ cudaError_t launch_pcg_start(PcgScalars* sc, const double* partial, int nrhs, do
 // Continuous batching: reset every column to inactive; start column `slot`
 // from the right-hand side b [rows] (r = b on free rows, x = p = 0).
 cudaError_t launch_batch_reset(PcgScalars* sc, double rtol, int maxit, cudaStream_t s);
-cudaError_t launch_batch_admit(const double* b, const uint8_t* row_free, double* r, float* r32,
-                               double* x, double* p, double* partial, PcgScalars* sc,
-                               int64_t rows, int nslots, int slot, cudaStream_t s);
+// Start columns first_slot .. first_slot + ncols - 1 of the batch from the
+// columns of b [rows][ldb].
+cudaError_t launch_batch_admit(const double* b, int ldb, const uint8_t* row_free, double* r,
+                               float* r32, double* x, double* p, double* partial, PcgScalars* sc,
+                               int64_t rows, int nslots, int first_slot, int ncols, cudaStream_t s);
+// out [rows] = column `slot` of v [rows][nslots].
+cudaError_t launch_column_gather(const double* v, double* out, int64_t rows, int nslots, int slot,
+                                 cudaStream_t s);
+// Repack the batch's x, r (and its FP32 copy) and p from [rows][old_slots] to
+// [rows][new_slots], column j taking old column m.s[j] (empty if < 0), through
+// tmp [rows * new_slots], which is left zero; the per-column scalars move with
+// their columns.
+struct SlotMap {
+  int s[kMaxRhs];
+};
+cudaError_t launch_batch_repack(double* x, double* r, float* r32, double* p, double* tmp,
+                                PcgScalars* sc, int64_t rows, int old_slots, int new_slots,
+                                const SlotMap& m, cudaStream_t s);
 template <typename TZ>
 cudaError_t launch_pcg_beta_p(PcgScalars* sc, const double* partial, const TZ* z, double* p,
                               int64_t rows, int nrhs, cudaStream_t s);

@@ -1525,8 +1525,29 @@ int nnmg_batch_admit(nnmg_handle* h, int slot, const double* b, int b_on_host, v
     NNMG_CUDA(cudaMemcpyAsync(h->pb, b, (size_t)L.rows * sizeof(double), cudaMemcpyHostToDevice, s));
     src = h->pb;
   }
-  NNMG_CUDA(launch_batch_admit(src, L.row_free, h->pr, h->pr32, h->px, h->pp, h->partial, h->sc,
-                               L.rows, h->batch_slots, slot, s));
+  NNMG_CUDA(launch_batch_admit(src, 1, L.row_free, h->pr, h->pr32, h->px, h->pp, h->partial, h->sc,
+                               L.rows, h->batch_slots, slot, 1, s));
+  return NNMG_OK;
+}
+
+int nnmg_batch_admit_cols(nnmg_handle* h, int first_slot, int ncols, const double* b, int ldb,
+                          int b_on_host, void* stream) {
+  if (!h || h->batch_mode < 0 || !b || ncols < 1 || first_slot < 0 ||
+      first_slot + ncols > h->batch_slots || ldb < ncols || (b_on_host && ldb > h->opt.max_nrhs)) {
+    set_error("nnmg_batch_admit_cols: no batch started, null b, slots outside the batch, "
+              "ldb < ncols or (host b) ldb > max_nrhs");
+    return NNMG_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevLevel& L = h->lv.back();
+  const double* src = b;
+  if (b_on_host) {
+    NNMG_CUDA(cudaMemcpyAsync(h->pb, b, (size_t)L.rows * ldb * sizeof(double),
+                              cudaMemcpyHostToDevice, s));
+    src = h->pb;
+  }
+  NNMG_CUDA(launch_batch_admit(src, ldb, L.row_free, h->pr, h->pr32, h->px, h->pp, h->partial,
+                               h->sc, L.rows, h->batch_slots, first_slot, ncols, s));
   return NNMG_OK;
 }
 
@@ -1546,6 +1567,34 @@ int nnmg_batch_step(nnmg_handle* h, int iterations, void* stream) {
   NNMG_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   NNMG_CUDA(cudaEventRecord(h->batch_ev, s));
   h->batch_inflight = true;
+  return NNMG_OK;
+}
+
+int nnmg_batch_repack(nnmg_handle* h, int new_slots, const int* src, void* stream) {
+  if (!h || h->batch_mode < 0 || !src || new_slots < 1 || new_slots > h->opt.max_nrhs) {
+    set_error("nnmg_batch_repack: no batch started, null src or new_slots not in 1..max_nrhs");
+    return NNMG_INVALID_ARG;
+  }
+  if (h->batch_inflight) {
+    set_error("nnmg_batch_repack: a step is in flight (poll until it reports ready)");
+    return NNMG_INVALID_ARG;
+  }
+  SlotMap m;
+  bool seen[kMaxRhs] = {};
+  for (int j = 0; j < kMaxRhs; ++j) m.s[j] = -1;
+  for (int j = 0; j < new_slots; ++j) {
+    const int q = src[j];
+    if (q < -1 || q >= h->batch_slots || (q >= 0 && seen[q])) {
+      set_error("nnmg_batch_repack: src entries must be distinct old slots or -1");
+      return NNMG_INVALID_ARG;
+    }
+    if (q >= 0) seen[q] = true;
+    m.s[j] = q;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  NNMG_CUDA(launch_batch_repack(h->px, h->pr, h->pr32, h->pp, h->pq, h->sc, h->lv.back().rows,
+                                h->batch_slots, new_slots, m, s));
+  h->batch_slots = new_slots;
   return NNMG_OK;
 }
 
@@ -1583,9 +1632,14 @@ int nnmg_batch_retire(nnmg_handle* h, int slot, double* x, int x_on_host, void* 
   }
   cudaStream_t s = (cudaStream_t)stream;
   const DevLevel& L = h->lv.back();
-  NNMG_CUDA(cudaMemcpy2DAsync(x, sizeof(double), h->px + slot, (size_t)h->batch_slots * sizeof(double),
-                              sizeof(double), (size_t)L.rows,
-                              x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  // the column is gathered on the device (a copy engine moves a column of
+  // 8-byte pieces slowly), then copied contiguously
+  if (x_on_host) {
+    NNMG_CUDA(launch_column_gather(h->px, h->pb, L.rows, h->batch_slots, slot, s));
+    NNMG_CUDA(cudaMemcpyAsync(x, h->pb, (size_t)L.rows * sizeof(double), cudaMemcpyDeviceToHost, s));
+  } else {
+    NNMG_CUDA(launch_column_gather(h->px, x, L.rows, h->batch_slots, slot, s));
+  }
   NNMG_CUDA(cudaMemsetAsync(&h->sc->active[slot], 0, sizeof(int), s));
   return NNMG_OK;
 }

@@ -17,7 +17,9 @@ The scheduler is host code; every arithmetic step runs in libnnmg's kernels.
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import ctypes as C
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -55,16 +57,61 @@ class FamilySpec:
     lame: tuple = (1.0, 1.0)
 
 
+_copy_pool = None
+COPY_THREADS = min(8, os.cpu_count() or 1)
+
+
+def parallel_copy(dst, src, chunk_bytes=8 << 20):
+    """dst[...] = src, split along the first axis into pieces of about
+    chunk_bytes copied by COPY_THREADS host threads (numpy copies release the
+    GIL): a request's right-hand sides and solutions are tens to hundreds of
+    MB, and one thread copies them at a fraction of the host's bandwidth."""
+    global _copy_pool
+    k = int(min(COPY_THREADS, max(1, dst.nbytes // chunk_bytes)))
+    if k <= 1:
+        np.copyto(dst, src)
+        return
+    if _copy_pool is None:
+        _copy_pool = concurrent.futures.ThreadPoolExecutor(max_workers=COPY_THREADS)
+    b = np.linspace(0, dst.shape[0], k + 1).astype(np.int64)
+    futs = [_copy_pool.submit(np.copyto, dst[lo:hi], src[lo:hi]) for lo, hi in zip(b[:-1], b[1:])]
+    for f in futs:
+        f.result()
+
+
+def batch_width(n, nslots):
+    """Columns of the batch that holds n occupied slots: 1 for n <= 1, else n
+    rounded up to an even count (paired FP32 kernels and 8-byte rows), at
+    most nslots."""
+    return 1 if n <= 1 else min(nslots, n + (n & 1))
+
+
+def pack_plan(owner, width, needed, nslots):
+    """How to repack a batch before a step: the occupied slots of
+    owner[:width] move, in order, to the first positions and the batch becomes
+    batch_width(needed) columns wide.  Returns (new_width, src) for
+    nnmg_batch_repack (src[j] = old slot of new column j, -1 empty), or None
+    if the batch already has that form."""
+    occ = [q for q in range(width) if owner[q] is not None]
+    w = batch_width(max(needed, len(occ)), nslots)
+    if w == width and occ == list(range(len(occ))):
+        return None
+    return w, occ + [-1] * (w - len(occ))
+
+
 class FamilyEngine:
     """One mesh family: cached hierarchy, own stream, 16-slot PCG.
 
     Right-hand sides and solutions pass through pinned per-slot staging
     buffers, so admission and retirement copies are asynchronous; the host
     waits once per poll.  When nothing is queued for the family, a step runs
-    up to `iters_per_step` iterations before the next host round trip."""
+    up to `iters_per_step` iterations before the next host round trip.
+    Before every step the occupied slots are packed into the first columns and
+    the batch is cut to the width they need (nnmg_batch_repack), because a
+    PCG iteration costs in proportion to its columns on the larger meshes."""
 
     def __init__(self, name, spec, nslots=16, mode=_abi.FP32_MG_FP64_CG, rtol=1e-8, maxit=200,
-                 iters_per_step=4):
+                 iters_per_step=4, warm_widths=True):
         import torch
         self.name = name
         self.spec = spec
@@ -82,9 +129,19 @@ class FamilyEngine:
         self.inflight = False
         self.last_used = time.perf_counter()
         self.iters_per_step = iters_per_step
-        self.b_stage = torch.empty(nslots, self.rows, dtype=torch.float64, pin_memory=True)
+        self.iterations = 0          # PCG iterations run by this engine
+        self.column_iterations = 0   # sum over those iterations of the occupied slots
+        self.width_iterations = 0    # sum over those iterations of the batch width
+        # pinned staging: a request's right-hand sides as one [rows][nrhs]
+        # block at the offset of its first slot; solutions one column per slot
+        self.b_stage = torch.empty(nslots * self.rows, dtype=torch.float64, pin_memory=True)
         self.x_stage = torch.empty(nslots, self.rows, dtype=torch.float64, pin_memory=True)
+        self.host_copy_s = 0.0       # host time spent staging b and x
         self._chk(self.lib.nnmg_batch_reset(self.H.h, mode, nslots, rtol, maxit, self.sptr), "reset")
+        self.width = nslots                   # columns of the device batch
+        self.repacks = 0
+        if warm_widths:
+            self._warm_widths()
         self._active = np.zeros(nslots, dtype=np.int32)
         self._iters = np.zeros(nslots, dtype=np.int32)
         self._rel = np.zeros(nslots)
@@ -111,27 +168,70 @@ class FamilyEngine:
     def busy(self):
         return self.inflight or any(o is not None for o in self.owner) or bool(self.queue)
 
+    def _warm_widths(self):
+        """Step every batch width twice with no column occupied, so that its
+        kernel choices are tuned and its iteration graph is captured before
+        serving (a width's first use would otherwise stall its requests)."""
+        ready = C.c_int(0)
+        for w in sorted({batch_width(n, self.nslots) for n in range(1, self.nslots + 1)}):
+            self._chk(self.lib.nnmg_batch_repack(self.H.h, w, (C.c_int * w)(*([-1] * w)),
+                                                 self.sptr), "repack")
+            self.width = w
+            for _ in range(2):
+                self._chk(self.lib.nnmg_batch_step(self.H.h, 1, self.sptr), "step")
+                self._chk(self.lib.nnmg_batch_poll(self.H.h, 1, C.byref(ready), None, None, None,
+                                                   None), "poll")
+
+    def _pack(self, needed):
+        plan = pack_plan(self.owner, self.width, needed, self.nslots)
+        if plan is None:
+            return
+        w, src = plan
+        arr = (C.c_int * w)(*src)
+        self._chk(self.lib.nnmg_batch_repack(self.H.h, w, arr, self.sptr), "repack")
+        self.owner = [self.owner[q] for q in src if q >= 0]
+        self.owner += [None] * (self.nslots - len(self.owner))
+        self.width = w
+        self.repacks += 1
+
     def admit(self, now):
-        """Move queued requests into free slots while whole requests fit."""
-        while self.queue and self.queue[0].nrhs <= self.free_slots():
-            req = self.queue.popleft()
+        """Move queued requests into free slots while whole requests fit, then
+        pack the batch to the width its columns need."""
+        take = []
+        free = self.free_slots()
+        while self.queue and self.queue[0].nrhs <= free:
+            take.append(self.queue.popleft())
+            free -= take[-1].nrhs
+        occupied = self.nslots - self.free_slots()
+        if occupied == 0 and not take:
+            return
+        self._pack(occupied + sum(r.nrhs for r in take))
+        for req in take:
+            m = req.nrhs
             req.t_admit = now
-            req.x = np.zeros((self.rows, req.nrhs))
-            req.iters = [0] * req.nrhs
-            req.relres = [0.0] * req.nrhs
-            req.status = [0] * req.nrhs
-            req.cols_left = req.nrhs
-            for j in range(req.nrhs):
-                slot = self.owner.index(None)
-                self.owner[slot] = (req, j)
-                self.b_stage[slot].numpy()[:] = req.b[:, j]
-                self._chk(self.lib.nnmg_batch_admit(self.H.h, slot, self.b_stage[slot].data_ptr(), 1,
-                                                    self.sptr), "admit")
+            req.x = np.zeros((m, self.rows)).T     # [rows, nrhs], columns contiguous
+            req.iters = [0] * m
+            req.relres = [0.0] * m
+            req.status = [0] * m
+            req.cols_left = m
+            s0 = self.owner.index(None)            # packed: the free slots follow
+            assert all(o is None for o in self.owner[s0:s0 + m])
+            for j in range(m):
+                self.owner[s0 + j] = (req, j)
+            t = time.perf_counter()
+            block = self.b_stage[s0 * self.rows:(s0 + m) * self.rows]
+            parallel_copy(block.numpy().reshape(self.rows, m), req.b)
+            self.host_copy_s += time.perf_counter() - t
+            self._chk(self.lib.nnmg_batch_admit_cols(self.H.h, s0, m, block.data_ptr(), m, 1,
+                                                     self.sptr), "admit")
 
     def step(self):
         if any(o is not None for o in self.owner) and not self.inflight:
             n = 1 if self.queue else self.iters_per_step
             self._chk(self.lib.nnmg_batch_step(self.H.h, n, self.sptr), "step")
+            self.iterations += n
+            self.column_iterations += n * sum(o is not None for o in self.owner)
+            self.width_iterations += n * self.width
             self.inflight = True
             self.last_used = time.perf_counter()
 
@@ -155,11 +255,15 @@ class FamilyEngine:
             self._chk(self.lib.nnmg_batch_retire(self.H.h, slot, self.x_stage[slot].data_ptr(), 1,
                                                  self.sptr), "retire")
             retired.append(slot)
+        t = time.perf_counter()
         if retired:
             self.stream.synchronize()                 # the retire copies
         for slot in retired:
             req, j = self.owner[slot]
-            req.x[:, j] = self.x_stage[slot].numpy()
+            parallel_copy(req.x[:, j], self.x_stage[slot].numpy())
+        self.host_copy_s += time.perf_counter() - t
+        for slot in retired:
+            req, j = self.owner[slot]
             req.iters[j] = int(self._iters[slot])
             req.relres[j] = float(self._rel[slot])
             req.status[j] = int(self._status[slot])

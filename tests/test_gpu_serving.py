@@ -65,6 +65,8 @@ def test_each_result_same_alone_and_in_the_mix(budget_gb):
     assert len(done) == len(reqs)
     if budget_gb is None:
         assert server.evictions > 0
+    else:                                   # the batches changed width on the way
+        assert sum(e.repacks for e in server.engines.values()) > 0
     for r in done:
         assert all(s == 0 for s in r.status) and max(r.relres) <= 1e-8
         xa, its = _alone(fams, r)
@@ -118,3 +120,93 @@ def test_a_waiting_family_allocates_nothing():
     ea.queue.clear()
     assert server.engine(b) is not None and server.evictions == 1
     server.close()
+
+
+def test_repack_continues_every_column():
+    """nnmg_batch_repack between steps: narrowing with a permutation that
+    drops columns, then widening and admitting into new columns (one column
+    from the device, two from a host block with nnmg_batch_admit_cols); every
+    continued column ends as its solve alone (relative L2 difference <= 1e-9,
+    iterations +-1).  Maps with repeated or out-of-range slots, widths outside
+    1..max_nrhs, a repack while a step is in flight and column blocks outside
+    the batch or with a bad leading dimension are rejected."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes as C
+    from paper_2412_10910_gb300 import _abi, nnmg
+    spec = _families()["2d_q3"]
+    H = nnmg.Hierarchy(spec.levels, spec.degree, cheb_degree=spec.cheb, max_nrhs=16)
+    lib = _abi.load()
+    top = H.n_levels - 1
+    rows = H.rows(top)
+    sp = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((rows, 7))
+    B[H.constrained(top)] = 0.0
+    bt = torch.tensor(B.T.copy(), device="cuda")          # bt[j] = column j
+    n = 16
+    active = np.zeros(n, dtype=np.int32)
+    iters = np.zeros(n, dtype=np.int32)
+    rel = np.zeros(n)
+    status = np.zeros(n, dtype=np.int32)
+
+    def ok(rc):
+        assert rc == _abi.OK, lib.nnmg_last_error()
+
+    def repack(src, width=None):
+        width = len(src) if width is None else width
+        return lib.nnmg_batch_repack(H.h, width, (C.c_int * max(1, len(src)))(*src), sp)
+
+    def step_and_poll(k):
+        ok(lib.nnmg_batch_step(H.h, k, sp))
+        ready = C.c_int(0)
+        ok(lib.nnmg_batch_poll(H.h, 1, C.byref(ready), active.ctypes.data, iters.ctypes.data,
+                               rel.ctypes.data, status.ctypes.data))
+        assert ready.value == 1
+
+    try:
+        ok(lib.nnmg_batch_reset(H.h, _abi.FP32_MG_FP64_CG, n, 1e-8, 200, sp))
+        for j in range(6):
+            ok(lib.nnmg_batch_admit(H.h, j, C.c_void_p(bt[j].data_ptr()), 0, sp))
+        step_and_poll(2)
+        assert np.all(active[:6] == 1)
+        # rejected maps: repeated slot, slot beyond the batch, widths 0 and 17
+        for src, width in (([0, 0], None), ([16], None), ([0], 0), (list(range(16)) + [-1], 17)):
+            assert repack(src, width) == _abi.INVALID_ARG
+        ok(lib.nnmg_batch_step(H.h, 1, sp))              # a step in flight
+        assert repack([0, 1]) == _abi.INVALID_ARG
+        ready = C.c_int(0)
+        ok(lib.nnmg_batch_poll(H.h, 1, C.byref(ready), None, None, None, None))
+        # narrow to 4 columns: old 5, 2, empty, old 0 (old 1, 3, 4 dropped)
+        ok(repack([5, 2, -1, 0]))
+        step_and_poll(2)
+        assert list(active[:4]) == [1, 1, 0, 1]
+        # widen to 6 columns: the three running ones, a new right-hand side in
+        # column 2 and, from a host block [rows][3], two more in columns 4-5
+        ok(repack([0, 1, -1, 3, -1, -1]))
+        ok(lib.nnmg_batch_admit(H.h, 2, C.c_void_p(bt[6].data_ptr()), 0, sp))
+        blk = np.ascontiguousarray(B[:, [1, 3, 4]])
+        for first, ncols, ldb in ((5, 2, 3), (4, 3, 2), (4, 2, 17)):
+            assert lib.nnmg_batch_admit_cols(H.h, first, ncols, blk.ctypes.data, ldb, 1, sp) == \
+                _abi.INVALID_ARG
+        ok(lib.nnmg_batch_admit_cols(H.h, 4, 2, blk.ctypes.data, 3, 1, sp))
+        for _ in range(200):
+            step_and_poll(1)
+            if not np.any(active[:6]):
+                break
+        assert np.all(status[:6] == 0) and np.all(rel[:6] <= 1e-8)
+        got = {}
+        for slot, col in ((0, 5), (1, 2), (2, 6), (3, 0), (4, 1), (5, 3)):
+            xs = torch.empty(rows, dtype=torch.float64, device="cuda")
+            ok(lib.nnmg_batch_retire(H.h, slot, C.c_void_p(xs.data_ptr()), 0, sp))
+            torch.cuda.synchronize()
+            got[col] = (xs.cpu().numpy(), int(iters[slot]))
+        for col, (xg, it) in got.items():
+            b1 = torch.tensor(B[:, col:col + 1], device="cuda")
+            x1 = torch.zeros_like(b1)
+            st, its, _ = H.pcg(b1, x1)
+            xa = x1.cpu().numpy()[:, 0]
+            assert np.linalg.norm(xg - xa) <= 1e-9 * np.linalg.norm(xa), col
+            assert abs(it - int(its[0])) <= 1, (col, it, its)
+    finally:
+        H.close()

@@ -7,7 +7,9 @@ uses (estimate_bytes, bytes, busy, close, last_used), so no GPU work is
 involved."""
 import pytest
 
-from paper_2412_10910_gb300.serving import Server
+import numpy as np
+
+from paper_2412_10910_gb300.serving import Server, batch_width, pack_plan, parallel_copy
 
 
 class FakeEngine:
@@ -82,3 +84,42 @@ def test_server_passes_the_solver_settings_to_its_engines():
     assert e.kw == {"nslots": 16, "mode": 1, "rtol": 1e-8, "maxit": 200}
     s.close()
     assert e.closed and not s.engines
+
+
+def test_batch_width_rounds_up_to_even_within_the_slots():
+    assert [batch_width(n, 16) for n in (0, 1, 2, 3, 8, 9, 15, 16, 17)] == \
+        [1, 1, 2, 4, 8, 10, 16, 16, 16]
+    assert batch_width(5, 4) == 4
+
+
+def test_pack_plan_moves_occupied_slots_first_and_sets_the_width():
+    A, B, Cq = object(), object(), object()
+    owner = [A, None, B, None, Cq] + [None] * 11
+    # three occupied of 16 columns: packed in order into 4 columns
+    assert pack_plan(owner, 16, 3, 16) == (4, [0, 2, 4, -1])
+    # room for two more columns being admitted: 5 -> 6 columns
+    assert pack_plan(owner, 16, 5, 16) == (6, [0, 2, 4, -1, -1, -1])
+    # already packed at the right width: nothing to do
+    packed = [A, B] + [None] * 14
+    assert pack_plan(packed, 2, 2, 16) is None
+    # packed, but a new request needs 7 more columns: widen, keep the order
+    assert pack_plan(packed, 2, 9, 16) == (10, [0, 1] + [-1] * 8)
+    # a retired column in front: the others move up even at the same width
+    assert pack_plan([None, A] + [None] * 14, 2, 1, 16) == (1, [1])
+    # never narrower than the occupied columns, never wider than the slots
+    assert pack_plan(owner, 16, 0, 16) == (4, [0, 2, 4, -1])
+    full = [A] * 16
+    assert pack_plan(full, 16, 20, 16) is None
+
+
+@pytest.mark.parametrize("shape", [(5,), (1000, 3), (700_001, 4)])
+def test_parallel_copy_equals_a_plain_copy(shape):
+    rng = np.random.default_rng(1)
+    src = rng.standard_normal(shape)
+    dst = np.zeros(shape)
+    parallel_copy(dst, src, chunk_bytes=1 << 16)
+    assert np.array_equal(dst, src)
+    col = np.zeros((shape[-1], shape[0])).T          # column-major destination
+    parallel_copy(col[:, 0] if col.ndim == 2 else col, src[:, 0] if src.ndim == 2 else src,
+                  chunk_bytes=1 << 12)
+    assert np.array_equal(col[:, 0] if col.ndim == 2 else col, src[:, 0] if src.ndim == 2 else src)
