@@ -103,7 +103,17 @@ typedef struct {
  * cheb_degree [3] Chebyshev steps per smoothing; smoothing_range [20] and
  * eig_safety [1.2] place the Chebyshev interval at
  * [eig_safety*lam/smoothing_range, eig_safety*lam] for lam the Lanczos
- * estimate after lanczos_steps [12] steps; max_nrhs [16] sizes work buffers. */
+ * estimate after lanczos_steps [12] steps; max_nrhs [16] sizes work buffers.
+ * deterministic [0] (no counterpart in the paper): 1 makes every result
+ * bitwise reproducible from run to run.  Each level's cells are colored
+ * greedily in input order so that no two cells of a color share a vertex,
+ * and stored grouped by color (input order within a color; the DoF numbering
+ * is that of the input order); the cell loops (operator, Jacobi diagonal,
+ * load vector) run one launch per color, so that every output entry receives
+ * at most one addition per launch and the additions' order is fixed.  Queries
+ * and inputs that are per cell (nnmg_cell_nodes, nnmg_quadrature_points, a
+ * load given per quadrature point) then use the stored order.  The persistent
+ * smoother is not used.  A mesh that needs more than 64 colors is BAD_MESH. */
 typedef struct {
   int degree;
   int n_components;
@@ -114,6 +124,7 @@ typedef struct {
   int lanczos_steps;
   double eig_safety;
   int max_nrhs;
+  int deterministic;
 } nnmg_options;
 
 /* Fill *opt with the defaults above. */
@@ -166,6 +177,20 @@ int nnmg_support_points(const nnmg_handle* h, int level, double* points);
 int nnmg_constrained_nodes(const nnmg_handle* h, int level, uint8_t* flags);
 int nnmg_cell_nodes(const nnmg_handle* h, int level, int32_t* cell_nodes);
 int nnmg_quadrature_points(const nnmg_handle* h, int level, double* xq);
+
+/* Cell colors of the deterministic mode (no counterpart in the paper).
+ * nnmg_color_cells (host only, no handle): greedy coloring of the cells
+ * [n_cells][2^dim] (vertex indices < n_vertices) in cell order, each cell
+ * taking the smallest color no earlier cell sharing a vertex took;
+ * color [n_cells] receives the colors, *n_colors their count.  INVALID_ARG
+ * for bad arguments or vertex indices, BAD_MESH if more than 64 colors would
+ * be needed.
+ * nnmg_level_colors: *n_colors of a level of a hierarchy (0 when it was not
+ * built deterministic) and, if color_start is not NULL, the first stored cell
+ * of every color and the cell count [n_colors + 1]. */
+int nnmg_color_cells(const int32_t* cells, int64_t n_cells, int64_t n_vertices, int dim,
+                     uint8_t* color, int* n_colors);
+int nnmg_level_colors(const nnmg_handle* h, int level, int64_t* color_start, int* n_colors);
 
 /* The located coarse cell and reference point of every free fine node of
  * level fine_level >= 1 (Sec. 3.1), in increasing fine node order:

@@ -23,7 +23,8 @@ class LevelDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("degree", C.c_int), ("n_components", C.c_int), ("lam", C.c_double),
                 ("mu", C.c_double), ("cheb_degree", C.c_int), ("smoothing_range", C.c_double),
-                ("lanczos_steps", C.c_int), ("eig_safety", C.c_double), ("max_nrhs", C.c_int)]
+                ("lanczos_steps", C.c_int), ("eig_safety", C.c_double), ("max_nrhs", C.c_int),
+                ("deterministic", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/nnmg.h
@@ -42,6 +43,9 @@ PROTOTYPES = {
     "nnmg_support_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_constrained_nodes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_cell_nodes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "nnmg_color_cells": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_void_p,
+                                   C.POINTER(C.c_int)]),
+    "nnmg_level_colors": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int)]),
     "nnmg_quadrature_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "nnmg_transfer_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "nnmg_pcg_device_loop": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),

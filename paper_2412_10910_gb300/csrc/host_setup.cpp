@@ -443,4 +443,40 @@ void build_buckets(const double* vertices, const int32_t* cells, int64_t nc, int
   }
 }
 
+// ------------------------------------------------------------ cell colors
+// Greedy coloring in cell order: a cell takes the smallest color that no
+// earlier cell sharing one of its vertices took.  Cells that share no vertex
+// share no node of a continuous Q_k space (edge, face and interior nodes
+// belong to the entities spanned by the cell's vertices), so the cells of one
+// color write disjoint output rows.  Returns the number of colors, or -1 if a
+// cell would need more than 64.
+int color_cells(const int32_t* cells, int64_t nc, int64_t nv, int dim, std::vector<uint8_t>* color) {
+  const int nvc = 1 << dim;
+  std::vector<int64_t> start((size_t)nv + 1, 0);
+  for (int64_t i = 0; i < nc * nvc; ++i) start[(size_t)cells[i] + 1]++;
+  for (int64_t v = 0; v < nv; ++v) start[(size_t)v + 1] += start[(size_t)v];
+  std::vector<int32_t> vcells((size_t)(nc * nvc));
+  std::vector<int64_t> fill(start.begin(), start.end() - 1);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int j = 0; j < nvc; ++j) vcells[(size_t)fill[(size_t)cells[c * nvc + j]]++] = (int32_t)c;
+  color->assign((size_t)nc, 0xff);
+  int ncolors = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    uint64_t used = 0;
+    for (int j = 0; j < nvc; ++j) {
+      const int32_t v = cells[c * nvc + j];
+      for (int64_t t = start[(size_t)v]; t < start[(size_t)v + 1]; ++t) {
+        const uint8_t k = (*color)[(size_t)vcells[(size_t)t]];
+        if (k != 0xff) used |= uint64_t(1) << k;
+      }
+    }
+    if (used == ~uint64_t(0)) return -1;
+    int k = 0;
+    while (used >> k & 1) ++k;
+    (*color)[(size_t)c] = (uint8_t)k;
+    ncolors = std::max(ncolors, k + 1);
+  }
+  return ncolors;
+}
+
 }  // namespace nnmg

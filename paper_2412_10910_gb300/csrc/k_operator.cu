@@ -1244,12 +1244,16 @@ cudaError_t launch_operator_impl(const DevLevel& L, const typename io_of<T>::typ
 template <typename T>
 cudaError_t launch_operator(const DevLevel& L, const T* x, T* y, int nrhs, double lambda,
                             double mu, cudaStream_t s, int units) {
-  return launch_operator_impl<T>(L, x, y, nrhs, lambda, mu, s, units);
+  return for_each_color(L, [&](const DevLevel& V) {
+    return launch_operator_impl<T>(V, x, y, nrhs, lambda, mu, s, units);
+  });
 }
 
 cudaError_t launch_operator_dw(const DevLevel& L, const double* x, double* y, int nrhs,
                                double lambda, double mu, cudaStream_t s, int units) {
-  return launch_operator_impl<dw>(L, x, y, nrhs, lambda, mu, s, units);
+  return for_each_color(L, [&](const DevLevel& V) {
+    return launch_operator_impl<dw>(V, x, y, nrhs, lambda, mu, s, units);
+  });
 }
 
 template <typename T>

@@ -416,7 +416,8 @@ cudaError_t launch_quad_points(const DevLevel& L, double* xq, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_diag(const DevLevel& L, double lambda, double mu, cudaStream_t s) {
+namespace {
+cudaError_t launch_diag_range(const DevLevel& L, double lambda, double mu, cudaStream_t s) {
   Basis1D<double> b64;
   Basis1D<float> b32;
   make_basis(L.k, &b64, &b32);
@@ -431,8 +432,8 @@ cudaError_t launch_diag(const DevLevel& L, double lambda, double mu, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_load_vector(const DevLevel& L, const double* f, int f_per_qp, double* b,
-                               int nrhs, int col, cudaStream_t s) {
+cudaError_t launch_load_range(const DevLevel& L, const double* f, int f_per_qp, double* b,
+                              int nrhs, int col, cudaStream_t s) {
   Basis1D<double> b64;
   Basis1D<float> b32;
   make_basis(L.k, &b64, &b32);
@@ -445,6 +446,20 @@ cudaError_t launch_load_vector(const DevLevel& L, const double* f, int f_per_qp,
     load_kernel<3><<<blocks_for(n, 128), 128, 0, s>>>(L.vertices, L.cells, L.cell_nodes, L.n_cells,
                                                       L.n1, L.ncomp, f, f_per_qp, b64, b, nrhs, col);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_diag(const DevLevel& L, double lambda, double mu, cudaStream_t s) {
+  return for_each_color(L, [&](const DevLevel& V) { return launch_diag_range(V, lambda, mu, s); });
+}
+
+// f per quadrature point is [n_cells][nloc][ncomp] in the level's cell order.
+cudaError_t launch_load_vector(const DevLevel& L, const double* f, int f_per_qp, double* b,
+                               int nrhs, int col, cudaStream_t s) {
+  return for_each_color(L, [&](const DevLevel& V) {
+    const double* fv = f_per_qp ? f + (V.cell_nodes - L.cell_nodes) * L.ncomp : f;
+    return launch_load_range(V, fv, f_per_qp, b, nrhs, col, s);
+  });
 }
 
 cudaError_t launch_locate(const DevLevel& coarse, const double* points, const int32_t* pt_nodes,

@@ -117,6 +117,10 @@ struct HostNumbering {
 int number_nodes(const int32_t* cells, int64_t nc, int64_t nv, int dim, int k,
                  const uint8_t* dirichlet_vertex, HostNumbering* out);
 
+// Greedy vertex-disjoint coloring of cells (at most 64 colors; -1 if more
+// would be needed), colors in [0, returned count).
+int color_cells(const int32_t* cells, int64_t nc, int64_t nv, int dim, std::vector<uint8_t>* color);
+
 struct BucketGeom {            // plain data, passed to the location kernel
   double lo[3], inv_w[3];
   int nb[3];
@@ -176,7 +180,58 @@ struct DevLevel {
   int32_t* free_rows = nullptr;      // [n_free_rows]
   double* coarse_inv = nullptr;      // [n_free_rows][n_free_rows]
   double* coarse_partial = nullptr;  // [kCoarseMaxSegments][n_free_rows][kMaxRhs]
+  // deterministic mode: cells stored grouped by color, no two cells of a
+  // color sharing a vertex; color c holds cells color_start[c] ..
+  // color_start[c+1]-1 (empty: cells in input order, one launch per loop)
+  std::vector<int64_t> color_start;
 };
+
+// Cells c0 .. c1-1 of L as a level of their own, for the cell-loop launchers
+// (operator, diagonal, load vector): the per-cell device arrays are offset,
+// node- and row-indexed arrays are shared, host data is not copied.
+inline void cell_range_view(const DevLevel& L, int64_t c0, int64_t c1, DevLevel* V) {
+  V->dim = L.dim;
+  V->k = L.k;
+  V->n1 = L.n1;
+  V->nloc = L.nloc;
+  V->ncomp = L.ncomp;
+  V->nmetric = L.nmetric;
+  V->nqp = L.nqp;
+  V->n_vertices = L.n_vertices;
+  V->n_nodes = L.n_nodes;
+  V->n_free_nodes = L.n_free_nodes;
+  V->rows = L.rows;
+  V->n_cells = c1 - c0;
+  V->vertices = L.vertices;
+  V->cells = L.cells ? L.cells + c0 * (1 << L.dim) : nullptr;
+  V->cell_nodes = L.cell_nodes ? L.cell_nodes + c0 * L.nloc : nullptr;
+  const int64_t mrow = (int64_t)L.nmetric * L.nqp;
+  V->metric64 = L.metric64 ? L.metric64 + c0 * mrow : nullptr;
+  V->metric32 = L.metric32 ? L.metric32 + c0 * mrow : nullptr;
+  V->metric_dw = L.metric_dw ? L.metric_dw + 2 * c0 * mrow : nullptr;
+  V->diag64 = L.diag64;
+  V->dinv64 = L.dinv64;
+  V->dinv32 = L.dinv32;
+  V->row_free = L.row_free;
+  V->points = L.points;
+}
+
+// Run launch(level) once, or once per color on the color's cell range (the
+// launches of one color add at most once into every output entry, so the
+// result does not depend on the order of the atomic additions).
+template <typename F>
+cudaError_t for_each_color(const DevLevel& L, F launch) {
+  if (L.color_start.empty()) return launch(L);
+  for (size_t c = 0; c + 1 < L.color_start.size(); ++c) {
+    const int64_t c0 = L.color_start[c], c1 = L.color_start[c + 1];
+    if (c1 == c0) continue;
+    DevLevel V;
+    cell_range_view(L, c0, c1, &V);
+    const cudaError_t e = launch(V);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 // ---------------------------------------------------------------- kernels
 // Launchers return cudaGetLastError() of the launch.

@@ -323,7 +323,7 @@ bool fused_smoother_allowed(const nnmg_handle* h, const DevLevel& L, int op_choi
                             int nrhs) {
   const char* e = getenv("NNMG_FUSED_SMOOTHER");    // read when a V-cycle is enqueued or captured
   const bool on = e && e[0] == '1';
-  return on && h->cooperative_ok && (op_choice == -1 || op_choice == 0) &&
+  return on && h->cooperative_ok && L.color_start.empty() && (op_choice == -1 || op_choice == 0) &&
          cheb_smoother_supported(L, m, nrhs);
 }
 
@@ -733,6 +733,32 @@ int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStrea
   const double t0 = wall_seconds();
   int rc = number_nodes(d.cells, d.n_cells, d.n_vertices, d.dim, L.k, d.dirichlet_vertex, &L.num);
   if (rc != NNMG_OK) return rc;
+  L.h_cells.assign(d.cells, d.cells + d.n_cells * nc4);
+  if (o.deterministic) {
+    // store the cells grouped by color (in input order within a color); the
+    // node numbering above stays that of the input order
+    std::vector<uint8_t> color;
+    const int nk = color_cells(d.cells, d.n_cells, d.n_vertices, d.dim, &color);
+    if (nk < 0) {
+      set_error("deterministic mode: a cell needs more than 64 colors");
+      return NNMG_BAD_MESH;
+    }
+    L.color_start.assign((size_t)nk + 1, 0);
+    for (auto k : color) L.color_start[(size_t)k + 1]++;
+    for (int k = 0; k < nk; ++k) L.color_start[(size_t)k + 1] += L.color_start[(size_t)k];
+    std::vector<int64_t> fill(L.color_start.begin(), L.color_start.end() - 1);
+    std::vector<int32_t> new_of((size_t)d.n_cells);
+    for (int64_t c = 0; c < d.n_cells; ++c) new_of[(size_t)c] = (int32_t)fill[color[(size_t)c]]++;
+    std::vector<int32_t> cn(L.num.cell_nodes.size());
+    for (int64_t c = 0; c < d.n_cells; ++c) {
+      const int64_t n = new_of[(size_t)c];
+      std::copy(d.cells + c * nc4, d.cells + (c + 1) * nc4, L.h_cells.begin() + n * nc4);
+      std::copy(L.num.cell_nodes.begin() + c * L.nloc, L.num.cell_nodes.begin() + (c + 1) * L.nloc,
+                cn.begin() + n * L.nloc);
+    }
+    L.num.cell_nodes.swap(cn);
+    for (auto& oc : L.num.owner_cell) oc = new_of[(size_t)oc];
+  }
   const double t1 = wall_seconds();
   h->setup_s[0] += t1 - t0;
   L.n_nodes = L.num.n_nodes;
@@ -740,11 +766,10 @@ int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStrea
   L.n_free_nodes = 0;
   for (auto c : L.num.constrained) L.n_free_nodes += c ? 0 : 1;
   L.h_vertices.assign(d.vertices, d.vertices + d.n_vertices * d.dim);
-  L.h_cells.assign(d.cells, d.cells + d.n_cells * nc4);
   CK(dalloc(h, &L.vertices, (size_t)d.n_vertices * d.dim));
   CK(dalloc(h, &L.cells, (size_t)d.n_cells * nc4));
   CK(cudaMemcpy(L.vertices, d.vertices, (size_t)d.n_vertices * d.dim * sizeof(double), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(L.cells, d.cells, (size_t)d.n_cells * nc4 * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.cells, L.h_cells.data(), (size_t)d.n_cells * nc4 * sizeof(int32_t), cudaMemcpyHostToDevice));
   std::vector<int32_t> masked(L.num.cell_nodes);
   for (auto& v : masked)
     if (L.num.constrained[v]) v = -1;
@@ -1021,6 +1046,7 @@ void nnmg_default_options(nnmg_options* o) {
   o->lanczos_steps = 12;
   o->eig_safety = 1.2;
   o->max_nrhs = 16;
+  o->deterministic = 0;
 }
 
 const char* nnmg_last_error(void) { return get_error(); }
@@ -1035,7 +1061,8 @@ int nnmg_setup_hierarchy(const nnmg_level_desc* levels, int n_levels, const nnmg
   *out = nullptr;
   if (opt->degree < 1 || opt->degree > kMaxDegree || (opt->n_components != 1 && opt->n_components != 3) ||
       opt->cheb_degree < 1 || opt->lanczos_steps < 1 || opt->max_nrhs < 1 || opt->max_nrhs > kMaxRhs ||
-      !(opt->smoothing_range > 1.0) || !(opt->eig_safety > 0.0)) {
+      !(opt->smoothing_range > 1.0) || !(opt->eig_safety > 0.0) ||
+      (opt->deterministic != 0 && opt->deterministic != 1)) {
     set_error("invalid options");
     return NNMG_INVALID_ARG;
   }
@@ -1198,6 +1225,39 @@ int nnmg_cell_nodes(const nnmg_handle* h, int level, int32_t* cn) {
   }
   const DevLevel& L = h->lv[level];
   std::memcpy(cn, L.num.cell_nodes.data(), L.num.cell_nodes.size() * sizeof(int32_t));
+  return NNMG_OK;
+}
+
+int nnmg_color_cells(const int32_t* cells, int64_t n_cells, int64_t n_vertices, int dim,
+                     uint8_t* color, int* n_colors) {
+  if (!cells || !color || !n_colors || n_cells < 0 || n_vertices < 1 || (dim != 2 && dim != 3)) {
+    set_error("nnmg_color_cells: bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < n_cells * (1 << dim); ++i)
+    if (cells[i] < 0 || cells[i] >= n_vertices) {
+      set_error("nnmg_color_cells: vertex index out of range");
+      return NNMG_INVALID_ARG;
+    }
+  std::vector<uint8_t> c;
+  const int nk = color_cells(cells, n_cells, n_vertices, dim, &c);
+  if (nk < 0) {
+    set_error("nnmg_color_cells: more than 64 colors needed");
+    return NNMG_BAD_MESH;
+  }
+  std::copy(c.begin(), c.end(), color);
+  *n_colors = nk;
+  return NNMG_OK;
+}
+
+int nnmg_level_colors(const nnmg_handle* h, int level, int64_t* color_start, int* n_colors) {
+  if (!h || !n_colors || level < 0 || level >= (int)h->lv.size()) {
+    set_error("bad argument");
+    return NNMG_INVALID_ARG;
+  }
+  const DevLevel& L = h->lv[level];
+  *n_colors = L.color_start.empty() ? 0 : (int)L.color_start.size() - 1;
+  if (color_start) std::copy(L.color_start.begin(), L.color_start.end(), color_start);
   return NNMG_OK;
 }
 

@@ -66,7 +66,7 @@ def nnmg_default_options():
 
 
 def _descs_and_options(levels, degree, n_components, lame, cheb_degree, smoothing_range,
-                       lanczos_steps, eig_safety, max_nrhs, level_degrees):
+                       lanczos_steps, eig_safety, max_nrhs, level_degrees, deterministic=False):
     keep = []
     descs = (_abi.LevelDesc * len(levels))()
     for i, lv in enumerate(levels):
@@ -82,18 +82,20 @@ def _descs_and_options(levels, degree, n_components, lame, cheb_degree, smoothin
     o.lam, o.mu = float(lame[0]), float(lame[1])
     o.cheb_degree, o.smoothing_range = int(cheb_degree), float(smoothing_range)
     o.lanczos_steps, o.eig_safety, o.max_nrhs = int(lanczos_steps), float(eig_safety), int(max_nrhs)
+    o.deterministic = 1 if deterministic else 0
     return descs, o, keep
 
 
 def nnmg_setup_hierarchy(levels, degree, n_components=1, lame=(1.0, 1.0), cheb_degree=3,
                          smoothing_range=20.0, lanczos_steps=12, eig_safety=1.2, max_nrhs=16,
-                         stream=None, level_degrees=None):
+                         stream=None, level_degrees=None, deterministic=False):
     """levels: sequence with .dim, .vertices [nv,dim] f64, .cells [nc,2^dim] i32, .dirichlet [nv] u8.
 
-    level_degrees: optional per-level degrees (0 = `degree`), coarse -> fine."""
+    level_degrees: optional per-level degrees (0 = `degree`), coarse -> fine.
+    deterministic: bitwise reproducible results (cells stored grouped by color)."""
     descs, o, keep = _descs_and_options(levels, degree, n_components, lame, cheb_degree,
                                         smoothing_range, lanczos_steps, eig_safety, max_nrhs,
-                                        level_degrees)
+                                        level_degrees, deterministic)
     h = C.c_void_p()
     _check(_lib.nnmg_setup_hierarchy(descs, len(levels), C.byref(o), _stream(stream), C.byref(h)),
            "nnmg_setup_hierarchy")
@@ -105,17 +107,40 @@ def nnmg_estimate_bytes(levels, degree, n_components=1, nrhs=16, level_degrees=N
     """(hierarchy bytes, solve bytes for nrhs columns) before anything is built
     (host only: no CUDA call)."""
     opts = dict(lame=(1.0, 1.0), cheb_degree=3, smoothing_range=20.0, lanczos_steps=12,
-                eig_safety=1.2, max_nrhs=16)
+                eig_safety=1.2, max_nrhs=16, deterministic=False)
     opts.update(kw)
     descs, o, keep = _descs_and_options(levels, degree, n_components, opts["lame"],
                                         opts["cheb_degree"], opts["smoothing_range"],
                                         opts["lanczos_steps"], opts["eig_safety"],
-                                        opts["max_nrhs"], level_degrees)
+                                        opts["max_nrhs"], level_degrees, opts["deterministic"])
     hb, sb = C.c_size_t(), C.c_size_t()
     _check(_lib.nnmg_estimate_bytes(descs, len(levels), C.byref(o), int(nrhs), C.byref(hb),
                                     C.byref(sb)), "nnmg_estimate_bytes")
     del keep
     return hb.value, sb.value
+
+
+def nnmg_color_cells(cells, n_vertices):
+    """Greedy vertex-disjoint cell colors (host only): (color [n_cells] u8, n_colors)."""
+    c = np.ascontiguousarray(cells, dtype=np.int32)
+    dim = {4: 2, 8: 3}[c.shape[1]]
+    color = np.zeros(c.shape[0], dtype=np.uint8)
+    n = C.c_int()
+    _check(_lib.nnmg_color_cells(c.ctypes.data, c.shape[0], int(n_vertices), dim, color.ctypes.data,
+                                 C.byref(n)), "nnmg_color_cells")
+    return color, n.value
+
+
+def nnmg_level_colors(h, level):
+    """First stored cell of every color and the cell count [n_colors + 1]
+    (empty if the hierarchy was not built deterministic)."""
+    n = C.c_int()
+    _check(_lib.nnmg_level_colors(h, level, None, C.byref(n)), "nnmg_level_colors")
+    if n.value == 0:
+        return np.zeros(0, dtype=np.int64)
+    out = np.zeros(n.value + 1, dtype=np.int64)
+    _check(_lib.nnmg_level_colors(h, level, out.ctypes.data, C.byref(n)), "nnmg_level_colors")
+    return out
 
 
 def nnmg_destroy(h):

@@ -50,10 +50,10 @@ def oracle_case(name):
     return levels, OracleHierarchy(levels, k, nc, lame, cheb, level_degrees=degrees(name))
 
 
-def gpu_case(name, levels):
+def gpu_case(name, levels, **kw):
     from paper_2412_10910_gb300 import nnmg
     _, k, nc, lame, cheb, nrhs = CASES[name][:6]
-    return nnmg.Hierarchy(levels, k, nc, lame, cheb, max_nrhs=16, level_degrees=degrees(name))
+    return nnmg.Hierarchy(levels, k, nc, lame, cheb, max_nrhs=16, level_degrees=degrees(name), **kw)
 
 
 def rng_vec(rows, nrhs, seed):

@@ -28,7 +28,16 @@ def test_default_options_host_only():
     o = _abi.Options()
     lib.nnmg_default_options(C.byref(o))
     assert (o.degree, o.cheb_degree, o.lanczos_steps, o.max_nrhs) == (1, 3, 12, 16)
-    assert o.smoothing_range == 20.0 and o.eig_safety == 1.2
+    assert o.smoothing_range == 20.0 and o.eig_safety == 1.2 and o.deterministic == 0
+
+
+def test_options_struct_matches_header():
+    """The ctypes mirror of nnmg_options has the header's fields in order."""
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct \{([^}]*)\} nnmg_options;", text).group(1)
+    fields = re.findall(r"(int|double)\s+(\w+);", body)
+    names = [n if n != "lambda" else "lam" for _, n in fields]
+    assert names == [f[0] for f in _abi.Options._fields_]
 
 
 def test_invalid_arguments_rejected_without_gpu_work():
@@ -42,6 +51,9 @@ def test_invalid_arguments_rejected_without_gpu_work():
     o.degree = 7
     d = (_abi.LevelDesc * 1)()
     assert lib.nnmg_setup_hierarchy(d, 1, C.byref(o), None, C.byref(h)) == _abi.INVALID_ARG
+    o.degree, o.deterministic = 1, 2
+    assert lib.nnmg_setup_hierarchy(d, 1, C.byref(o), None, C.byref(h)) == _abi.INVALID_ARG
+    assert b"invalid options" in lib.nnmg_last_error()
     assert lib.nnmg_n_levels(None) == 0 and lib.nnmg_hierarchy_bytes(None) == 0
 
 
