@@ -292,8 +292,11 @@ int nnmg_set_nested(nnmg_handle* h, int fine_level, const int32_t* parent_cell,
  * variable NNMG_FUSED_SMOOTHER=1 each smoothing sweep of a small level served
  * by the register operator runs as one persistent cooperative kernel (grid
  * barriers between its operator and vector phases; not used by handles in
- * continuous batching); by default every step is its own kernel, which
- * measured faster inside the captured graph. */
+ * continuous batching).  With NNMG_FUSED_STEP=1 each Chebyshev step with an
+ * operator pass on such a level is one launch without any wait (the cells add
+ * A x, count themselves done on every node, and the block that completes a
+ * node's count updates that node).  By default every step is an operator
+ * kernel and a vector kernel, which measured faster than both. */
 int nnmg_vcycle(nnmg_handle* h, int precision, const void* r, void* z, int nrhs,
                 void* stream);
 

@@ -655,6 +655,66 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) op_reg_kernel(
   op_reg_unit<D, K, T>(cell_nodes, metric, x, y, cell, (int)(u - cell * nrhs), nrhs, B);
 }
 
+// ------------------------------------------------- operator + Chebyshev step
+// One Chebyshev-Jacobi step (Sec. 4 smoother) in one launch without any wait:
+// the register kernel adds t += A_K x for the block's cells; then the block
+// counts, per cell and node, one finished cell on cnt[node].  A count that
+// reaches valence[node] (the number of cells holding the node) means the
+// node's row of A x is complete: the block lists the node and, after a
+// barrier, applies the step to the listed rows, one (node, right-hand side)
+// element per thread: d = cd d + cr D^-1 (f - t), x += d, t = 0, cnt = 0.
+// x at a node changes only after every cell holding the node has gathered
+// it.  Blocks hold whole cells (blockDim = cells per block x nrhs).
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) op_cheb_kernel(
+    const int32_t* __restrict__ cell_nodes, const T* __restrict__ metric, const T* __restrict__ f,
+    T* __restrict__ t, const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x,
+    int32_t* __restrict__ cnt, const int32_t* __restrict__ valence, int64_t n_cells, int nrhs,
+    Basis1D<T> B, T cd, T cr) {
+  pdl_trigger();
+  pdl_wait();
+  constexpr int N = K + 1;
+  constexpr int NQ = D == 2 ? N * N : N * N * N;
+  __shared__ int32_t done[128 * NQ];   // nodes this block completes (at most its cell slots)
+  __shared__ int n_done;
+  const int cells_per_block = blockDim.x / nrhs;
+  const int64_t c0 = (int64_t)blockIdx.x * cells_per_block;
+  const int64_t cell = c0 + threadIdx.x / nrhs;
+  if (threadIdx.x == 0) n_done = 0;
+  if (cell < n_cells)
+    op_reg_unit<D, K, T>(cell_nodes, metric, x, t, cell, (int)(threadIdx.x % nrhs), nrhs, B);
+  // release: the block's additions (ordered before this thread by the
+  // barrier) before this thread's counts; acquire: a node's counts before the
+  // block's reads of its t.  Acquire-release fences, not the sequentially
+  // consistent __threadfence().
+  __syncthreads();
+  fence_acq_rel_gpu();
+  const int64_t nc = n_cells - c0 < cells_per_block ? n_cells - c0 : cells_per_block;
+  for (int i = threadIdx.x; i < nc * NQ; i += blockDim.x) {
+    const int dof = cell_nodes[c0 * NQ + i];
+    if (dof >= 0 && atomicAdd(&cnt[dof], 1) == valence[dof] - 1) done[atomicAdd(&n_done, 1)] = dof;
+  }
+  fence_acq_rel_gpu();
+  __syncthreads();
+  fence_acq_rel_gpu();
+  // the completed nodes' rows, one (node, right-hand side) element per thread
+  const int ne = n_done * nrhs;
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+    const int64_t dof = done[i / nrhs];
+    const int64_t e = dof * nrhs + i % nrhs;
+    const T fe = f[e], te = __ldcg(&t[e]), de = d[e], xe = x[e], di = dinv[dof];
+    const T dn = cd * de + cr * di * (fe - te);
+    d[e] = dn;
+    x[e] = xe + dn;
+    t[e] = T(0);
+    if (i % nrhs == 0) cnt[dof] = 0;
+  }
+}
+
 // ------------------------------------------------------ persistent smoother
 // One Chebyshev-Jacobi smoothing sweep (Sec. 4) in a single cooperative
 // launch: the operator phase t = A x (the register kernel's cell body over a
@@ -1255,6 +1315,38 @@ cudaError_t launch_operator_dw(const DevLevel& L, const double* x, double* y, in
     return launch_operator_impl<dw>(V, x, y, nrhs, lambda, mu, s, units);
   });
 }
+
+bool cheb_step_fused_supported(const DevLevel& L) {
+  return L.color_start.empty() && L.ncomp == 1 && L.valence && L.node_count &&
+         ((L.dim == 3 && L.k <= 2) || (L.dim == 2 && L.k <= 4));
+}
+
+template <typename T>
+cudaError_t launch_cheb_step_fused(const DevLevel& L, const T* f, T* t, const T* dinv, T* d, T* x,
+                                   double cd, double cr, int nrhs, cudaStream_t s) {
+  if (!cheb_step_fused_supported(L) || nrhs < 1 || nrhs > 128) return cudaErrorInvalidValue;
+  if (L.n_cells == 0) return cudaSuccess;
+  const int cpb = 128 / nrhs;
+  const unsigned blocks = (unsigned)((L.n_cells + cpb - 1) / cpb);
+  const T* m = metric_of<T>(L);
+  Basis1D<T> B;
+#define NNMG_OPCHEB(DD, KK)                                                                   \
+  if (L.dim == DD && L.k == KK) {                                                            \
+    pick_basis<T>(KK, &B);                                                                   \
+    return launch_k(op_cheb_kernel<DD, KK, T>, blocks, cpb * nrhs, 0, s, L.cell_nodes, m, f, t, \
+                    dinv, d, x, L.node_count, L.valence, L.n_cells, nrhs, B, (T)cd, (T)cr);  \
+  }
+  NNMG_OPCHEB(2, 1) NNMG_OPCHEB(2, 2) NNMG_OPCHEB(2, 3) NNMG_OPCHEB(2, 4)
+  NNMG_OPCHEB(3, 1) NNMG_OPCHEB(3, 2)
+#undef NNMG_OPCHEB
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_cheb_step_fused<float>(const DevLevel&, const float*, float*,
+                                                   const float*, float*, float*, double, double,
+                                                   int, cudaStream_t);
+template cudaError_t launch_cheb_step_fused<double>(const DevLevel&, const double*, double*,
+                                                    const double*, double*, double*, double,
+                                                    double, int, cudaStream_t);
 
 template <typename T>
 int operator_unit_candidates(const DevLevel& L, int nrhs, int* out, int max_out) {

@@ -157,6 +157,8 @@ struct DevLevel {
   float* dinv32 = nullptr;
   uint8_t* row_free = nullptr;       // [rows]
   double* points = nullptr;          // [n_nodes][dim]
+  int32_t* valence = nullptr;        // [n_nodes] cells holding the node (0 if constrained)
+  int32_t* node_count = nullptr;     // [n_nodes] finished cells of a fused step (0 at rest)
   double lam_max = 0.0;
   double cheb_a = 0.0, cheb_b = 0.0;
   // transfer from the next coarser level (this level is the fine one), l >= 1
@@ -214,6 +216,8 @@ inline void cell_range_view(const DevLevel& L, int64_t c0, int64_t c1, DevLevel*
   V->dinv32 = L.dinv32;
   V->row_free = L.row_free;
   V->points = L.points;
+  V->valence = L.valence;
+  V->node_count = L.node_count;
 }
 
 // Run launch(level) once, or once per color on the color's cell range (the
@@ -311,6 +315,13 @@ struct SmootherPlan {
 };
 // Whether launch_cheb_smoother serves this level with m steps and nrhs columns.
 bool cheb_smoother_supported(const DevLevel& L, int m, int nrhs);
+// One Chebyshev step with its operator pass in one launch (Poisson levels the
+// register kernel serves, not in the deterministic mode): t += A x, then at
+// every node whose cells are all done d = cd d + cr D^-1 (f - t), x += d, t = 0.
+bool cheb_step_fused_supported(const DevLevel& L);
+template <typename T>
+cudaError_t launch_cheb_step_fused(const DevLevel& L, const T* f, T* t, const T* dinv, T* d, T* x,
+                                   double cd, double cr, int nrhs, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cheb_smoother(const DevLevel& L, const T* f, T* t, const T* dinv, T* d, T* x,
                                  int nrhs, const SmootherPlan& P, unsigned* bar, int* err,

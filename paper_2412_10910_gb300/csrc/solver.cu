@@ -327,6 +327,15 @@ bool fused_smoother_allowed(const nnmg_handle* h, const DevLevel& L, int op_choi
          cheb_smoother_supported(L, m, nrhs);
 }
 
+// The fused operator + Chebyshev step (opt-in: NNMG_FUSED_STEP=1 in the
+// environment; measured slower than the operator and vector kernels apart)
+// serves a level where the register kernel is the operator choice.
+bool fused_step_allowed(const DevLevel& L, int op_choice) {
+  const char* e = getenv("NNMG_FUSED_STEP");          // read when a V-cycle is enqueued or captured
+  const bool on = e && e[0] == '1';
+  return on && (op_choice == -1 || op_choice == 0) && cheb_step_fused_supported(L);
+}
+
 // Chebyshev coefficients of one sweep (Sec. 4 smoother; the recurrence of
 // the kernel-per-step path): pre-smoothing from zero, or continuing from x.
 SmootherPlan smoother_plan(const DevLevel& L, int m, bool pre) {
@@ -390,12 +399,18 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
       RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
           launch_cheb_init<T>(f, dinv, d, x, 1.0 / theta, L.rows, nrhs, s));
       double rho = 1.0 / sigma;
+      const bool fs = fused_step_allowed(L, ou);
       for (int j = 1; j < m; ++j) {
-        RUN(l, NNMG_PROF_PRE, NNMG_PROF_OPERATOR,
-            launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
         const double rn = 1.0 / (2.0 * sigma - rho);
-        RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
-            launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
+        if (fs) {
+          RUN(l, NNMG_PROF_PRE, NNMG_PROF_OPERATOR,
+              launch_cheb_step_fused<T>(L, f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, nrhs, s));
+        } else {
+          RUN(l, NNMG_PROF_PRE, NNMG_PROF_OPERATOR,
+              launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+          RUN(l, NNMG_PROF_PRE, NNMG_PROF_VECTOR,
+              launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
+        }
         rho = rn;
       }
       RUN(l, NNMG_PROF_RESIDUAL, NNMG_PROF_OPERATOR,
@@ -434,16 +449,24 @@ cudaError_t enqueue_vcycle(nnmg_handle* h, const T* f_top, int nrhs, cudaStream_
       continue;
     }
     double rho = 1.0 / sigma;
-    RUN(l, NNMG_PROF_POST, NNMG_PROF_OPERATOR, launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
-    RUN(l, NNMG_PROF_POST, NNMG_PROF_VECTOR,
-        launch_cheb_step<T>(f, t, dinv, d, x, 0.0, 1.0 / theta, L.rows, nrhs, s));
-    for (int j = 1; j < m; ++j) {
-      RUN(l, NNMG_PROF_POST, NNMG_PROF_OPERATOR,
-          launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
-      const double rn = 1.0 / (2.0 * sigma - rho);
-      RUN(l, NNMG_PROF_POST, NNMG_PROF_VECTOR,
-          launch_cheb_step<T>(f, t, dinv, d, x, rn * rho, 2.0 * rn / delta, L.rows, nrhs, s));
-      rho = rn;
+    const bool fs = fused_step_allowed(L, ou);
+    for (int j = 0; j < m; ++j) {
+      double cd = 0.0, cr = 1.0 / theta;
+      if (j > 0) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        cd = rn * rho;
+        cr = 2.0 * rn / delta;
+        rho = rn;
+      }
+      if (fs) {
+        RUN(l, NNMG_PROF_POST, NNMG_PROF_OPERATOR,
+            launch_cheb_step_fused<T>(L, f, t, dinv, d, x, cd, cr, nrhs, s));
+      } else {
+        RUN(l, NNMG_PROF_POST, NNMG_PROF_OPERATOR,
+            launch_operator<T>(L, x, t, nrhs, lam, mu, s, ou));
+        RUN(l, NNMG_PROF_POST, NNMG_PROF_VECTOR,
+            launch_cheb_step<T>(f, t, dinv, d, x, cd, cr, L.rows, nrhs, s));
+      }
     }
   }
 #undef RUN
@@ -779,6 +802,17 @@ int setup_level(nnmg_handle* h, const nnmg_level_desc& d, DevLevel& L, cudaStrea
   CK(dalloc(h, &L.owner_local, (size_t)L.n_nodes));
   CK(cudaMemcpy(L.owner_cell, L.num.owner_cell.data(), L.n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(L.owner_local, L.num.owner_local.data(), L.n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
+  {
+    // cells holding each free node, and the zeroed counts of the fused
+    // operator + Chebyshev step
+    std::vector<int32_t> val((size_t)L.n_nodes, 0);
+    for (auto v : masked)
+      if (v >= 0) val[(size_t)v]++;
+    CK(dalloc(h, &L.valence, (size_t)L.n_nodes));
+    CK(dalloc(h, &L.node_count, (size_t)L.n_nodes));
+    CK(cudaMemcpy(L.valence, val.data(), L.n_nodes * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemset(L.node_count, 0, L.n_nodes * sizeof(int32_t)));
+  }
   std::vector<uint8_t> rf((size_t)L.rows);
   for (int64_t r = 0; r < L.rows; ++r) rf[r] = L.num.constrained[r / L.ncomp] ? 0 : 1;
   CK(dalloc(h, &L.row_free, (size_t)L.rows));
@@ -1000,7 +1034,7 @@ size_t planned_hierarchy_bytes(const std::vector<LevelPlan>& P) {
     const LevelPlan& L = P[l];
     const int64_t nm = L.n_cells * L.nmetric * ((L.nloc + 3) / 4 * 4);
     b += bytes_of<double>(L.n_vertices * L.dim) + bytes_of<int32_t>(L.n_cells << L.dim) +
-         bytes_of<int32_t>(L.n_cells * L.nloc) + 2 * bytes_of<int32_t>(L.n_nodes) +
+         bytes_of<int32_t>(L.n_cells * L.nloc) + 4 * bytes_of<int32_t>(L.n_nodes) +
          bytes_of<uint8_t>(L.rows) + bytes_of<double>(nm) + bytes_of<float>(nm) +
          bytes_of<double>(L.n_nodes * L.dim) + 2 * bytes_of<double>(L.rows) + bytes_of<float>(L.rows);
     if (l >= 1) {

@@ -190,3 +190,36 @@ def test_vcycle_and_pcg_with_and_without_persistent_smoother(name, monkeypatch):
         finally:
             H.close()
     assert its["1"] == its["0"]
+
+
+@pytest.mark.parametrize("name", ["c1_q3", "c1_q4_5rhs", "c1_q2_16rhs", "c2_q2_3lev", "c3_q4_pmg"])
+def test_fused_chebyshev_step_on_and_off(name, monkeypatch):
+    """The Chebyshev steps as one operator + update launch (NNMG_FUSED_STEP=1)
+    and as separate operator and vector kernels (the default): V-cycles in
+    FP64 and FP32 against the oracle's, repeated (the per-node counts must be
+    back at zero after every step), and against each other."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    levels, O = oracle_case(name)
+    nrhs = CASES[name][5]
+    top = len(O.levels) - 1
+    r = rng_vec(O.levels[top].n, nrhs, 41)
+    r[np.repeat(O.levels[top].constrained, O.ncomp)] = 0.0
+    zo = O.vcycle(r, "fp64")
+    zo32 = O.vcycle(r.astype(np.float32).astype(np.float64), "fp32")
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("NNMG_FUSED_STEP", flag)
+        H = gpu_case(name, levels)
+        try:
+            for _ in range(3):                                 # eager, captured, replayed
+                z = H.vector(top, nrhs)
+                H.vcycle(torch.tensor(r, device="cuda"), z)
+                assert _relmax(z.cpu().numpy(), zo) <= 1e-9, flag
+                z32 = H.vector(top, nrhs, torch.float32)
+                H.vcycle(torch.tensor(r, dtype=torch.float32, device="cuda"), z32)
+                assert _relmax(z32.double().cpu().numpy(), zo32) <= 2e-5, flag
+            out[flag] = z.cpu().numpy()
+        finally:
+            H.close()
+    assert _relmax(out["1"], out["0"]) <= 1e-12
