@@ -473,6 +473,14 @@ def run_nested_cube(args, rank):
 
 def run_serving(args, rank):
     """Serving mix: 12 cached mesh families, Poisson arrivals, continuous batching."""
+    line = serving_mix(args.requests, args.rate)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serving_mix(n_requests, fixed_rate=0.0):
+    """The serving mix's line: calibration burst, then n_requests Poisson
+    arrivals at fixed_rate (0: 0.8 x the calibrated service rate)."""
     import numpy as np
     import torch
     from paper_2412_10910_gb300.serving import FamilySpec, Request, Server, latency_stats
@@ -494,16 +502,16 @@ def run_serving(args, rank):
         return out
 
     # calibration: a closed burst (all requests at t = 0) gives the service rate
-    ncal = max(24, args.requests // 20)
+    ncal = max(60, n_requests // 20)
     cal = make(serving_requests(fams, ncal, seed=7, rate=1e9))
     t = time.perf_counter()
     server.run(cal)
     cal_rate = ncal / (time.perf_counter() - t)
-    rate = args.rate if args.rate else 0.8 * cal_rate
+    rate = fixed_rate if fixed_rate else 0.8 * cal_rate
     for e in server.engines.values():          # occupancy of the timed run only
         e.iterations = e.column_iterations = e.width_iterations = 0
         e.host_copy_s = 0.0
-    reqs = make(serving_requests(fams, args.requests, seed=6, rate=rate))
+    reqs = make(serving_requests(fams, n_requests, seed=6, rate=rate))
     t = time.perf_counter()
     done = server.run(reqs)
     span = time.perf_counter() - t
@@ -534,10 +542,12 @@ def run_serving(args, rank):
             "config": {"workload": "serving mix: 12 jittered non-nested families (seed 5), "
                                    "Poisson arrivals (seed 6), 1-16 N(0,1) RHS, FP32 V-cycle / "
                                    "FP64 CG to 1e-8, continuous batching over 16 slots per family"}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     server.close()
+    return line
 
+
+# requests of the serving mix appended to the full line
+SERVING_REQUESTS = 600
 
 # FMA-chain iterations per probe launch (about 50 ms each on GB300)
 PROBE_ITERS = {0: 4000, 1: 200000, 2: 100000}
@@ -579,6 +589,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave the shortened serving mix out of the full line")
     ap.add_argument("--only", choices=["solve", "solve64", "solvedw", "vcycle", "op64", "op32",
                                        "opdw", "prolong", "restrict", "serving", "configs", "peaks"],
                     default=None, help="run only one timed section (for profiler launch lists), "
@@ -828,9 +840,18 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(8)
+    H.close()
+    if rank == 0 and world == 1 and not args.no_serving:
+        # the serving mix, shortened, after the timed solves (north-star
+        # serving item; `--only serving` runs the 2000-request mix)
+        sv = serving_mix(SERVING_REQUESTS)
+        line["serving"] = {k: sv[k] for k in ("metric", "value", "unit", "requests",
+                                             "arrival_rate_per_s", "calibration_rate_per_s",
+                                             "makespan_s", "latency", "all_converged",
+                                             "setup_s_12_families")}
+        line["serving"]["workload"] = sv["config"]["workload"]
     if rank == 0:
         print(json.dumps(line), flush=True)
-    H.close()
     if world > 1:
         dist.destroy_process_group()
 
