@@ -61,7 +61,7 @@ _copy_pool = None
 COPY_THREADS = min(8, os.cpu_count() or 1)
 
 
-def parallel_copy(dst, src, chunk_bytes=8 << 20):
+def parallel_copy(dst, src, chunk_bytes=2 << 20):
     """dst[...] = src, split along the first axis into pieces of about
     chunk_bytes copied by COPY_THREADS host threads (numpy copies release the
     GIL): a request's right-hand sides and solutions are tens to hundreds of
@@ -137,6 +137,8 @@ class FamilyEngine:
         self.b_stage = torch.empty(nslots * self.rows, dtype=torch.float64, pin_memory=True)
         self.x_stage = torch.empty(nslots, self.rows, dtype=torch.float64, pin_memory=True)
         self.host_copy_s = 0.0       # host time spent staging b and x
+        self.pending = collections.deque()     # (event, retired columns) in stream order
+        self.staged = [False] * nslots         # x_stage[slot] awaits its host copy
         self._chk(self.lib.nnmg_batch_reset(self.H.h, mode, nslots, rtol, maxit, self.sptr), "reset")
         self.width = nslots                   # columns of the device batch
         self.repacks = 0
@@ -166,7 +168,8 @@ class FamilyEngine:
         return sum(o is None for o in self.owner)
 
     def busy(self):
-        return self.inflight or any(o is not None for o in self.owner) or bool(self.queue)
+        return (self.inflight or any(o is not None for o in self.owner) or bool(self.queue)
+                or bool(self.pending))
 
     def _warm_widths(self):
         """Step every batch width twice with no column occupied, so that its
@@ -235,45 +238,64 @@ class FamilyEngine:
             self.inflight = True
             self.last_used = time.perf_counter()
 
+    def _drain(self, block=False):
+        """Finish the retirements whose device copies are done: solution
+        columns from the staging buffers into the requests; returns the
+        requests that are complete."""
+        done = []
+        while self.pending and (block or self.pending[0][0].query()):
+            ev, cols = self.pending.popleft()
+            ev.synchronize()
+            t = time.perf_counter()
+            for slot, req, j, its, rel, st in cols:
+                parallel_copy(req.x[:, j], self.x_stage[slot].numpy())
+                self.staged[slot] = False
+                req.iters[j], req.relres[j], req.status[j] = its, rel, st
+                req.cols_left -= 1
+                if req.cols_left == 0:
+                    done.append(req)
+            self.host_copy_s += time.perf_counter() - t
+        return done
+
     def poll(self, wait=False):
-        """If the last step finished: retire finished columns; returns finished requests."""
+        """Finish earlier retirements whose copies are done and, if the last
+        step finished, retire its converged columns: their slots are free at
+        once, their solutions arrive asynchronously (an event after the copies;
+        the host does not wait for the GPU).  Returns the requests completed,
+        or None if nothing happened."""
+        import torch
+        done = self._drain()
         if not self.inflight:
-            return None
+            return done or None
         ready = C.c_int(0)
         self._chk(self.lib.nnmg_batch_poll(self.H.h, int(wait), C.byref(ready),
                                            self._active.ctypes.data, self._iters.ctypes.data,
                                            self._rel.ctypes.data, self._status.ctypes.data),
                   "poll")
         if not ready.value:
-            return None
+            return done or None
         self.inflight = False
-        done = []
-        retired = []
+        cols = []
         for slot, o in enumerate(self.owner):
             if o is None or self._active[slot]:
                 continue
+            if self.staged[slot]:                     # an earlier copy into this buffer
+                done += self._drain(block=True)
             self._chk(self.lib.nnmg_batch_retire(self.H.h, slot, self.x_stage[slot].data_ptr(), 1,
                                                  self.sptr), "retire")
-            retired.append(slot)
-        t = time.perf_counter()
-        if retired:
-            self.stream.synchronize()                 # the retire copies
-        for slot in retired:
-            req, j = self.owner[slot]
-            parallel_copy(req.x[:, j], self.x_stage[slot].numpy())
-        self.host_copy_s += time.perf_counter() - t
-        for slot in retired:
-            req, j = self.owner[slot]
-            req.iters[j] = int(self._iters[slot])
-            req.relres[j] = float(self._rel[slot])
-            req.status[j] = int(self._status[slot])
+            req, j = o
+            cols.append((slot, req, j, int(self._iters[slot]), float(self._rel[slot]),
+                         int(self._status[slot])))
+            self.staged[slot] = True
             self.owner[slot] = None
-            req.cols_left -= 1
-            if req.cols_left == 0:
-                done.append(req)
+        if cols:
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            self.pending.append((ev, cols))
         return done
 
     def close(self):
+        self._drain(block=True)
         self.H.close()
 
 
