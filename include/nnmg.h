@@ -112,8 +112,10 @@ typedef struct {
  * load vector) run one launch per color, so that every output entry receives
  * at most one addition per launch and the additions' order is fixed.  Queries
  * and inputs that are per cell (nnmg_cell_nodes, nnmg_quadrature_points, a
- * load given per quadrature point) then use the stored order.  The persistent
- * smoother is not used.  A mesh that needs more than 64 colors is BAD_MESH. */
+ * load given per quadrature point) then use the stored order.  The operator
+ * kernels follow the fixed default rule (no timed choice, which could differ
+ * between two hierarchies), and the persistent smoother is not used.  A mesh
+ * that needs more than 64 colors is BAD_MESH. */
 typedef struct {
   int degree;
   int n_components;

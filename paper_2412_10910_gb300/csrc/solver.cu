@@ -187,7 +187,8 @@ int ensure_pcg(nnmg_handle* h) {
 // per block, -100 - U its paired FP32 form, 0 the default rule.  On first use
 // every legal choice is timed (two warm-ups and six timed launches on scratch
 // vectors, CUDA events) and the fastest is kept for the handle's lifetime.
-// Never runs during stream capture (the default rule is used then);
+// Never runs during stream capture or in the deterministic mode (the default
+// rule is used then);
 // NNMG_AUTOTUNE=0 in the environment keeps the default rule, NNMG_OP_CHOICE=<c>
 // forces choice c on every level (a choice that does not apply to a level
 // falls back to the default there).
@@ -206,7 +207,10 @@ int tune_units(nnmg_handle* h, int level, int prec_key, int nrhs, cudaStream_t s
     return !(e && e[0] == '0');
   }();
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (!enabled || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+  // the deterministic mode keeps the default rule: a choice made by timing
+  // could differ between two hierarchies and with it the rounding
+  if (!enabled || h->opt.deterministic || cudaStreamIsCapturing(s, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone)
     return 0;
   const DevLevel& L = h->lv[level];
   int cand[16];
