@@ -842,8 +842,8 @@ def main():
         line["cpu_baseline"] = cpu_baseline_sample(8)
     H.close()
     if rank == 0 and world == 1 and not args.no_serving:
-        # the serving mix, shortened, after the timed solves (north-star
-        # serving item; `--only serving` runs the 2000-request mix)
+        # the serving mix, shortened, after the timed solves (`--only
+        # serving` runs the 2000-request mix)
         sv = serving_mix(SERVING_REQUESTS)
         line["serving"] = {k: sv[k] for k in ("metric", "value", "unit", "requests",
                                              "arrival_rate_per_s", "calibration_rate_per_s",
